@@ -1,0 +1,136 @@
+/*
+ * mmvm.h - C ABI of the GB300 multi-moment vortex method (MMVM) library.
+ *
+ * The library evaluates and integrates the moment ODE of Uminsky, Wayne &
+ * Barbaro, "A multi-moment vortex method for 2D viscous fluids"
+ * (arXiv:1010.2475):
+ *
+ *   omega(x,t) = sum_j sum_{|k|<=M} M^j[k1,k2](t) D^k phi_00(x - x^j(t); lambda(t))
+ *       (eq:vorticity_decomposition, eq:moment_expansion_def_tw0)
+ *   phi_00(x; lambda) = exp(-|x|^2/lambda^2) / (pi lambda^2),
+ *   lambda(t)^2 = lambda_0^2 + 4 nu t                        (eq:phi00)
+ *   dM^j_k/dt = A + B + C                                  (eq:Final_CrossCoef)
+ *   dx^j/dt from eq:xjdot_Final (the self pair excluded, eq:xjdot)
+ *
+ * Conventions shared by every entry point:
+ *  - n particles, truncation order M (k1 + k2 <= M), K = (M+1)(M+2)/2.
+ *  - Positions x: n x 2 float64, row-major (x^j_1, x^j_2).
+ *  - Moments: n x K float64, row-major; moment (k1,k2) of particle j sits at
+ *    column q(k1+k2) + k2 with q(s) = s(s+1)/2 (grouped by total order, then by
+ *    k2).  Column 0 is the circulation M^j[0,0], which must be nonzero for
+ *    every particle (eq:mass).
+ *  - The separation between particles is s_{j,j'} = x^j - x^{j'} (eq:xjdotA).
+ *  - All particles share one core size lambda (the sqrt(2) lambda kernel of
+ *    eq:Fullint needs equal cores); viscosity enters only through lambda(t).
+ *  - Host pointers are read or written synchronously before the call
+ *    returns.  "Device" pointers are CUDA global-memory pointers on the
+ *    context's device; such calls are ordered on the context's stream and
+ *    return before the GPU work ends (use mmvm_synchronize).
+ *  - Return value: 0 (MMVM_OK), a positive value (MMVM_PENDING) or a negative
+ *    error code below; mmvm_last_error() gives a message for the calling
+ *    thread's last failure.
+ *  - A context is not thread-safe: one thread at a time per context.
+ */
+#ifndef MMVM_H_
+#define MMVM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MMVM_OK 0
+#define MMVM_PENDING 1
+#define MMVM_E_INVALID_ARG (-1)       /* null pointer, bad size, bad enum       */
+#define MMVM_E_ZERO_CIRCULATION (-2)  /* some M^j[0,0] == 0 (eq:mass)           */
+#define MMVM_E_UNSUPPORTED (-3)       /* order above the compiled limit         */
+#define MMVM_E_OOM (-4)               /* device allocation failed / over budget */
+#define MMVM_E_NUMERIC (-5)           /* non-finite value in the state          */
+#define MMVM_E_TIMEOUT (-6)           /* a bounded device wait ran out          */
+#define MMVM_E_DEVICE (-7)            /* CUDA runtime error                     */
+
+/* Arithmetic of the pair interaction (the all-pairs part of A, B and C).
+ * Coefficient tables, the state, RK4, the centroid and circulation sums and
+ * the per-particle finish are FP64 in every mode.                           */
+#define MMVM_FP64 0        /* pair jets and contractions in FP64              */
+#define MMVM_MIXED_FP32 1  /* pair jets and contractions in FP32, sums of
+                              source tiles carried as FP32 (hi, lo) pairs     */
+
+/* Largest order of the all-pairs kernels (jets of order 3M).  Single
+ * particles (n == 1) accept any order up to MMVM_MAX_ORDER_SINGLE.          */
+#define MMVM_MAX_ORDER_PAIRS 8
+#define MMVM_MAX_ORDER_SINGLE 16
+
+typedef struct mmvm_config {
+  int32_t order;        /* truncation order M >= 0                            */
+  int32_t precision;    /* MMVM_FP64 or MMVM_MIXED_FP32                       */
+  double lambda0;       /* core size lambda_0 > 0 at t = 0 (eq:phi00)        */
+  double nu;            /* kinematic viscosity >= 0 (Re = Gamma_ref / nu)     */
+  int32_t device;       /* CUDA device ordinal                                */
+  uint32_t flags;       /* reserved, must be 0                                */
+} mmvm_config;
+
+typedef struct mmvm_ctx mmvm_ctx;
+
+/* Create a context on cfg->device.  *out receives the handle; the caller
+ * destroys it with mmvm_destroy.  Errors: INVALID_ARG, UNSUPPORTED, DEVICE.  */
+int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out);
+
+/* Release every device buffer of the context.  NULL is ignored.             */
+void mmvm_destroy(mmvm_ctx* ctx);
+
+/* Load a state from HOST memory: n particles, x (n x 2), moments (n x K),
+ * time t.  The library copies the data into device memory it owns (buffers
+ * grow as needed).  Errors: INVALID_ARG (n < 1, null pointers),
+ * ZERO_CIRCULATION, NUMERIC (NaN/Inf), UNSUPPORTED (n > 1 with
+ * order > MMVM_MAX_ORDER_PAIRS), OOM, DEVICE.                               */
+int mmvm_set_state(mmvm_ctx* ctx, int64_t n, const double* x, const double* moments,
+                   double t);
+
+/* Same, from DEVICE pointers (copied device-to-device on the context stream;
+ * the caller may reuse its buffers once the call returns... after
+ * mmvm_synchronize).  The zero-circulation / finiteness checks are not made. */
+int mmvm_set_state_device(mmvm_ctx* ctx, int64_t n, const double* d_x,
+                          const double* d_moments, double t);
+
+/* Copy the current state to HOST memory (x: n x 2, moments: n x K, *t).
+ * Any of the three pointers may be NULL to skip it.  Synchronises.          */
+int mmvm_get_state(mmvm_ctx* ctx, double* x, double* moments, double* t);
+
+/* Copy the current state to DEVICE memory (asynchronous on the stream).      */
+int mmvm_get_state_device(mmvm_ctx* ctx, double* d_x, double* d_moments);
+
+/* Right-hand side at the current state (eq:Final_CrossCoef, eq:xjdot_Final):
+ * dxdt (n x 2) and dMdt (n x K) written to HOST memory.  Synchronises.      */
+int mmvm_rhs(mmvm_ctx* ctx, double* dxdt, double* dMdt);
+
+/* Right-hand side written to DEVICE memory (asynchronous on the stream).     */
+int mmvm_rhs_device(mmvm_ctx* ctx, double* d_dxdt, double* d_dMdt);
+
+/* Advance the state by nsteps classic RK4 steps of size dt, lambda evaluated
+ * at the stage times.  Asynchronous on the context stream (the steps are
+ * replayed from a CUDA graph); mmvm_get_state or mmvm_synchronize waits.     */
+int mmvm_step(mmvm_ctx* ctx, double dt, int64_t nsteps);
+
+/* Use this CUDA stream (a cudaStream_t, NULL = the context's own stream).    */
+int mmvm_set_stream(mmvm_ctx* ctx, void* stream);
+
+/* Wait for the context's queued work; reports asynchronous device errors.    */
+int mmvm_synchronize(mmvm_ctx* ctx);
+
+/* Number of particles, order, moments per particle of the loaded state.      */
+int64_t mmvm_num_particles(const mmvm_ctx* ctx);
+int32_t mmvm_num_moments(int32_t order);
+
+/* Kernel launches issued by this context since creation (for accounting).   */
+int64_t mmvm_launch_count(const mmvm_ctx* ctx);
+
+/* Message for the calling thread's last error ("" if none).                 */
+const char* mmvm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMVM_H_ */

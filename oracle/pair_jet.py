@@ -99,42 +99,46 @@ def _hermite(kmax: int, y: np.ndarray) -> np.ndarray:
 
 
 def _far(s: np.ndarray, P: int, c: float):
-    """Far regime: point-vortex jet minus the Leibniz product with exp(-|b|^2/c)."""
+    """Far regime: point-vortex jet minus the Leibniz product with exp(-|b|^2/c).
+
+    Taylor-normalised arrays (entry alpha divided by alpha1! alpha2!) turn the
+    two-variable Leibniz rule into a truncated two-dimensional convolution;
+    D^gamma E = e1[gamma1] e2[gamma2] factorises per axis, so the convolution is
+    evaluated as two nested one-dimensional sums (lower-triangular Toeplitz
+    products) per pair.
+    """
     npair = s.shape[0]
     z = s[:, 0] + 1j * s[:, 1]
     fact = np.array([math.factorial(n) for n in range(P + 1)], dtype=np.float64)
     ar = np.arange(P + 1)
-    # g_n = (-i/2pi) (-1)^n n! / z^{n+1}
+    A1, A2 = np.meshgrid(ar, ar, indexing="ij")
+    inside = (A1 + A2) <= P
+    # g_n = (-i/2pi) (-1)^n n! / z^{n+1};  D^a (V1 - i V2)_pv = i^{a2} g_{|a|}
     g = (-1j / (2.0 * math.pi)) * ((-1.0) ** ar * fact)[None, :] / z[:, None] ** (ar[None, :] + 1)
-    # Taylor-normalised point-vortex jet: PV[a1,a2] / (a1! a2!)
-    pv1 = np.zeros((npair, P + 1, P + 1))
-    pv2 = np.zeros((npair, P + 1, P + 1))
-    for a1 in range(P + 1):
-        for a2 in range(P + 1 - a1):
-            v = (1j) ** a2 * g[:, a1 + a2]
-            pv1[:, a1, a2] = v.real / (fact[a1] * fact[a2])
-            pv2[:, a1, a2] = -v.imag / (fact[a1] * fact[a2])
+    nidx = np.where(inside, A1 + A2, 0)
+    v = g[:, nidx] * ((1j) ** A2)[None] * inside[None]
+    tay = 1.0 / (fact[:, None] * fact[None, :])
+    pv1 = v.real * tay[None]
+    pv2 = -v.imag * tay[None]
     x = (s[:, 0] ** 2 + s[:, 1] ** 2) / c
     tail = x < X_NO_TAIL
     if np.any(tail):
         rc = math.sqrt(c)
         ii = np.nonzero(tail)[0]
-        h1 = _hermite(P, s[ii, 0] / rc)
-        h2 = _hermite(P, s[ii, 1] / rc)
-        ex = np.exp(-x[ii])
-        # Taylor-normalised D^a E = c^{-|a|/2} (-1)^{|a|} H_a1 H_a2 e^{-x} / (a1! a2!)
-        scale = ((-1.0) ** (ar[:, None] + ar[None, :]) * c ** (-(ar[:, None] + ar[None, :]) / 2.0)
-                 / (fact[:, None] * fact[None, :]))
-        et = h1[:, :, None] * h2[:, None, :] * ex[:, None, None] * scale[None]
-        corr1 = np.zeros((ii.size, P + 1, P + 1))
-        corr2 = np.zeros((ii.size, P + 1, P + 1))
-        for b1 in range(P + 1):
-            for b2 in range(P + 1 - b1):
-                e = et[:, : P + 1 - b1, : P + 1 - b2]
-                corr1[:, b1:, b2:] += pv1[ii, b1, b2][:, None, None] * e
-                corr2[:, b1:, b2:] += pv2[ii, b1, b2][:, None, None] * e
-        pv1[ii] -= corr1
-        pv2[ii] -= corr2
+        ex1 = np.exp(-(s[ii, 0] / rc) ** 2)
+        ex2 = np.exp(-(s[ii, 1] / rc) ** 2)
+        # e_d[k] = c^{-k/2} d^k/dt^k exp(-t^2) / k! at t = b_d / sqrt(c)
+        sc = ((-1.0) ** ar * c ** (-ar / 2.0) / fact)[None, :]
+        e1 = _hermite(P, s[ii, 0] / rc) * ex1[:, None] * sc
+        e2 = _hermite(P, s[ii, 1] / rc) * ex2[:, None] * sc
+        toe = np.clip(A1 - A2, 0, None)
+        low = (A1 >= A2)[None]
+        T1 = e1[:, toe] * low          # T1[p, a1, b1] = e1[a1 - b1]
+        T2 = e2[:, toe] * low          # T2[p, a2, b2] = e2[a2 - b2]
+        for pv in (pv1, pv2):
+            inner = np.matmul(pv[ii], np.swapaxes(T2, 1, 2))   # [b1, a2]
+            corr = np.matmul(T1, inner)                        # [a1, a2]
+            pv[ii] -= corr * inside[None]
     mi = multi_indices(P)
     J1 = np.empty((npair, len(mi)))
     J2 = np.empty((npair, len(mi)))

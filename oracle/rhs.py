@@ -98,27 +98,40 @@ def rhs_literal(x, mom, t, order, lam0, nu):
     return xdot, dM
 
 
-@lru_cache(maxsize=32)
-def _finish_terms(order: int, lam: float):
-    """(k, l, coef, comp, offset-column) lists of the (i,q) sums, with c_k folded in.
+@lru_cache(maxsize=16)
+def _finish_terms_unit(order: int):
+    """(k, l, coef at lambda = 1, lambda power, comp, offset column) of the (i,q) sums.
 
-    dM_k gets sum_l M_l sum_terms coef * W_comp[offset]; the offsets index the
-    velocity jet W up to order 2M - 1.
+    Every term of c_k * Gamma^I/II (eq:coefficient, eq:FinalSingleI/II) is a
+    power of lambda times a number: c_k ~ lambda^{2|k|}, the bracketed ratios
+    ~ lambda^{-2(i+1)-2q} (I) or lambda^{-2i-2(q+1)} (II); both give
+    lambda^{2|k| - 2(i+q+1)}.
     """
-    ks, ls, cs, comps, offs = [], [], [], [], []
+    ks, ls, cs, pw, comps, offs = [], [], [], [], [], []
     for ki, (k1, k2) in enumerate(multi_indices(order)):
-        ck = c_k(k1, k2, lam)
+        ck = c_k(k1, k2, 1.0)
         for li, (l1, l2) in enumerate(multi_indices(order)):
-            for comp, terms in ((0, gamma_I_terms(k1, k2, l1, l2, lam)),
-                                (1, gamma_II_terms(k1, k2, l1, l2, lam))):
+            for comp, terms in ((0, gamma_I_terms(k1, k2, l1, l2, 1.0)),
+                                (1, gamma_II_terms(k1, k2, l1, l2, 1.0))):
                 for coef, (o1, o2) in terms:
+                    # offset o = k + l - 2(i+q) - 1 in total order
+                    iq1 = (k1 + k2 + l1 + l2 - (o1 + o2) - 1) // 2 + 1
                     ks.append(ki)
                     ls.append(li)
                     cs.append(ck * coef)
+                    pw.append(2 * (k1 + k2) - 2 * iq1)
                     comps.append(comp)
                     offs.append(idx(o1, o2))
-    return (np.array(ks, dtype=np.int64), np.array(ls, dtype=np.int64),
-            np.array(cs), np.array(comps, dtype=np.int64), np.array(offs, dtype=np.int64))
+    return (np.array(ks, dtype=np.int64), np.array(ls, dtype=np.int64), np.array(cs),
+            np.array(pw, dtype=np.int64), np.array(comps, dtype=np.int64),
+            np.array(offs, dtype=np.int64))
+
+
+def _finish_terms(order: int, lam: float):
+    """(k, l, coef, comp, offset-column) of the (i,q) sums at core size lambda,
+    with c_k folded in: dM_k gets sum_l M_l sum_terms coef * W_comp[offset]."""
+    ks, ls, cs, pw, comps, offs = _finish_terms_unit(order)
+    return ks, ls, cs * lam ** pw.astype(np.float64), comps, offs
 
 
 @lru_cache(maxsize=16)

@@ -1,0 +1,242 @@
+"""Python binding of the GB300 MMVM library (libmmvm.so, C ABI in include/mmvm.h).
+
+Argument marshalling only: every step of the right-hand side and of the RK4
+integration runs in the library's CUDA kernels.  If libmmvm.so has not been
+built (``python -m paper_1010_2475_gb300.build``) every call raises; there is
+no CPU fallback.
+
+The functions keep the C names (``mmvm_create``, ``mmvm_set_state``, ...).
+Host arrays are float64 numpy arrays; the ``*_device`` variants take raw CUDA
+pointers (for example ``torch.Tensor.data_ptr()`` of float64 CUDA tensors on
+the context's device).  ``Context`` wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmmvm.so")
+
+MMVM_OK = 0
+MMVM_PENDING = 1
+MMVM_E_INVALID_ARG = -1
+MMVM_E_ZERO_CIRCULATION = -2
+MMVM_E_UNSUPPORTED = -3
+MMVM_E_OOM = -4
+MMVM_E_NUMERIC = -5
+MMVM_E_TIMEOUT = -6
+MMVM_E_DEVICE = -7
+MMVM_FP64 = 0
+MMVM_MIXED_FP32 = 1
+MMVM_MAX_ORDER_PAIRS = 8
+MMVM_MAX_ORDER_SINGLE = 16
+
+_ERRNAMES = {
+    MMVM_E_INVALID_ARG: "INVALID_ARG",
+    MMVM_E_ZERO_CIRCULATION: "ZERO_CIRCULATION",
+    MMVM_E_UNSUPPORTED: "UNSUPPORTED",
+    MMVM_E_OOM: "OOM",
+    MMVM_E_NUMERIC: "NUMERIC",
+    MMVM_E_TIMEOUT: "TIMEOUT",
+    MMVM_E_DEVICE: "DEVICE",
+}
+
+# Every symbol include/mmvm.h declares (checked by the ABI test).
+EXPORTS = (
+    "mmvm_create", "mmvm_destroy", "mmvm_set_state", "mmvm_set_state_device",
+    "mmvm_get_state", "mmvm_get_state_device", "mmvm_rhs", "mmvm_rhs_device",
+    "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
+    "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error",
+)
+
+
+class MMVMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mmvm_config(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("lambda0", ctypes.c_double), ("nu", ctypes.c_double),
+                ("device", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+_lib_handle = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmmvm.so (raises if it is missing: there is no fallback)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_1010_2475_gb300.build` (CUDA toolkit needed)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.mmvm_create.argtypes = [ctypes.POINTER(mmvm_config), ctypes.POINTER(P)]
+    lib.mmvm_create.restype = ctypes.c_int
+    lib.mmvm_destroy.argtypes = [P]
+    lib.mmvm_destroy.restype = None
+    lib.mmvm_set_state.argtypes = [P, ctypes.c_int64, D, D, ctypes.c_double]
+    lib.mmvm_set_state.restype = ctypes.c_int
+    lib.mmvm_set_state_device.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_double]
+    lib.mmvm_set_state_device.restype = ctypes.c_int
+    lib.mmvm_get_state.argtypes = [P, D, D, D]
+    lib.mmvm_get_state.restype = ctypes.c_int
+    lib.mmvm_get_state_device.argtypes = [P, P, P]
+    lib.mmvm_get_state_device.restype = ctypes.c_int
+    lib.mmvm_rhs.argtypes = [P, D, D]
+    lib.mmvm_rhs.restype = ctypes.c_int
+    lib.mmvm_rhs_device.argtypes = [P, P, P]
+    lib.mmvm_rhs_device.restype = ctypes.c_int
+    lib.mmvm_step.argtypes = [P, ctypes.c_double, ctypes.c_int64]
+    lib.mmvm_step.restype = ctypes.c_int
+    lib.mmvm_set_stream.argtypes = [P, P]
+    lib.mmvm_set_stream.restype = ctypes.c_int
+    lib.mmvm_synchronize.argtypes = [P]
+    lib.mmvm_synchronize.restype = ctypes.c_int
+    lib.mmvm_num_particles.argtypes = [P]
+    lib.mmvm_num_particles.restype = ctypes.c_int64
+    lib.mmvm_num_moments.argtypes = [ctypes.c_int32]
+    lib.mmvm_num_moments.restype = ctypes.c_int32
+    lib.mmvm_launch_count.argtypes = [P]
+    lib.mmvm_launch_count.restype = ctypes.c_int64
+    lib.mmvm_last_error.argtypes = []
+    lib.mmvm_last_error.restype = ctypes.c_char_p
+    _lib_handle = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc < 0:
+        msg = load_library().mmvm_last_error()
+        raise MMVMError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def n_moments(order: int) -> int:
+    return (order + 1) * (order + 2) // 2
+
+
+def mmvm_create(order: int, lambda0: float, nu: float, precision: int = MMVM_FP64,
+                device: int = 0) -> ctypes.c_void_p:
+    cfg = mmvm_config(order, precision, lambda0, nu, device, 0)
+    h = ctypes.c_void_p()
+    _check(load_library().mmvm_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def mmvm_destroy(h) -> None:
+    load_library().mmvm_destroy(h)
+
+
+def mmvm_set_state(h, x: np.ndarray, moments: np.ndarray, t: float) -> None:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    moments = np.ascontiguousarray(moments, dtype=np.float64)
+    if x.ndim != 2 or x.shape[1] != 2 or moments.ndim != 2 or moments.shape[0] != x.shape[0]:
+        raise ValueError("x must be (n, 2) and moments (n, K)")
+    _check(load_library().mmvm_set_state(h, x.shape[0], _dptr(x), _dptr(moments), float(t)))
+
+
+def mmvm_set_state_device(h, n: int, d_x: int, d_moments: int, t: float) -> None:
+    _check(load_library().mmvm_set_state_device(h, n, ctypes.c_void_p(d_x),
+                                                ctypes.c_void_p(d_moments), float(t)))
+
+
+def mmvm_get_state(h, order: int):
+    lib = load_library()
+    n = lib.mmvm_num_particles(h)
+    x = np.empty((n, 2))
+    m = np.empty((n, n_moments(order)))
+    t = ctypes.c_double()
+    _check(lib.mmvm_get_state(h, _dptr(x), _dptr(m), ctypes.byref(t)))
+    return x, m, t.value
+
+
+def mmvm_get_state_device(h, d_x: int, d_moments: int) -> None:
+    _check(load_library().mmvm_get_state_device(h, ctypes.c_void_p(d_x), ctypes.c_void_p(d_moments)))
+
+
+def mmvm_rhs(h, order: int):
+    lib = load_library()
+    n = lib.mmvm_num_particles(h)
+    dx = np.empty((n, 2))
+    dm = np.empty((n, n_moments(order)))
+    _check(lib.mmvm_rhs(h, _dptr(dx), _dptr(dm)))
+    return dx, dm
+
+
+def mmvm_rhs_device(h, d_dx: int, d_dm: int) -> None:
+    _check(load_library().mmvm_rhs_device(h, ctypes.c_void_p(d_dx), ctypes.c_void_p(d_dm)))
+
+
+def mmvm_step(h, dt: float, nsteps: int) -> None:
+    _check(load_library().mmvm_step(h, float(dt), int(nsteps)))
+
+
+def mmvm_set_stream(h, stream: Optional[int]) -> None:
+    _check(load_library().mmvm_set_stream(h, ctypes.c_void_p(stream or 0)))
+
+
+def mmvm_synchronize(h) -> None:
+    _check(load_library().mmvm_synchronize(h))
+
+
+def mmvm_launch_count(h) -> int:
+    return int(load_library().mmvm_launch_count(h))
+
+
+class Context:
+    """Owning wrapper of an mmvm_ctx handle."""
+
+    def __init__(self, order: int, lambda0: float, nu: float, precision: int = MMVM_FP64,
+                 device: int = 0):
+        self.order = order
+        self.handle = mmvm_create(order, lambda0, nu, precision, device)
+
+    def set_state(self, x, moments, t=0.0):
+        mmvm_set_state(self.handle, x, moments, t)
+
+    def get_state(self):
+        return mmvm_get_state(self.handle, self.order)
+
+    def rhs(self):
+        return mmvm_rhs(self.handle, self.order)
+
+    def step(self, dt, nsteps=1):
+        mmvm_step(self.handle, dt, nsteps)
+
+    def synchronize(self):
+        mmvm_synchronize(self.handle)
+
+    @property
+    def launches(self) -> int:
+        return mmvm_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            mmvm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,441 @@
+// C-ABI of the MMVM library (declarations and contracts in include/mmvm.h).
+//
+// One right-hand-side evaluation is three launches on the context stream:
+//   prep   (core size at the stage time, FP32/FP64 source records),
+//   pair   (all-pairs stream-function correlation, skipped for n == 1),
+//   finish (FP64: chunk sum, self pair, centroid, moment equation, RK4 stage).
+// An RK4 step is four evaluations plus a one-thread time advance; the step is
+// captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mmvm.h"
+#include "common.cuh"
+#include "pair_registry.h"
+#include "particle_kernels.h"
+#include "tables.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? MMVM_E_OOM : MMVM_E_DEVICE;
+}
+
+#define MMVM_CK(expr)                                  \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
+  } while (0)
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;  // elements
+  cudaError_t ensure(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) cap = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+}  // namespace
+
+struct mmvm_ctx {
+  mmvm_config cfg{};
+  int M = 0, K = 0, NB = 0;
+  int64_t n = 0;
+  cudaStream_t own = nullptr, st = nullptr;
+  DevBuf<double> x, m, xs, ms, xsum, msum, rdx, rdm, scal, partial;
+  DevBuf<unsigned char> rec;
+  DevBuf<int> flags, k_off, e_l, e_b;
+  DevBuf<double> e_c, psi0;
+  mmvm::PairEntry pe;
+  int S = 32;            // sources per shared-memory tile
+  int chunks = 1;        // source chunks of the pair kernel
+  int finish_tb = 1;     // targets per finish block
+  bool graph_ok = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t launches = 0;
+
+  double* t_dev() { return scal.p; }
+  double* dt_dev() { return scal.p + 1; }
+
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    gexec = nullptr;
+    graph = nullptr;
+    graph_ok = false;
+  }
+};
+
+namespace {
+
+int choose_chunks(const mmvm_ctx* c, int64_t n) {
+  if (n <= 1) return 0;
+  int dev_sms = 0;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
+  int per_sm = 1;
+  if (c->pe.occupancy) c->pe.occupancy(c->S, &per_sm);
+  per_sm = std::max(per_sm, 1);
+  const int64_t tiles = (n + c->pe.tpc - 1) / c->pe.tpc;
+  const int64_t slots = (int64_t)std::max(dev_sms, 1) * per_sm;
+  // at least ~4 waves of CTAs, chunks no shorter than 4 tiles of sources
+  int64_t ch = (4 * slots + tiles - 1) / tiles;
+  const int64_t max_ch = std::max<int64_t>(1, n / (4 * c->S));
+  ch = std::min(std::max<int64_t>(ch, 1), max_ch);
+  return (int)ch;
+}
+
+int ensure_buffers(mmvm_ctx* c, int64_t n) {
+  const size_t K = c->K;
+  bool realloc = false;
+  auto grow = [&](auto& b, size_t cnt) -> cudaError_t {
+    if (cnt > b.cap || !b.p) realloc = true;
+    return b.ensure(cnt);
+  };
+  MMVM_CK(grow(c->x, 2 * n));
+  MMVM_CK(grow(c->m, K * n));
+  MMVM_CK(grow(c->xs, 2 * n));
+  MMVM_CK(grow(c->ms, K * n));
+  MMVM_CK(grow(c->xsum, 2 * n));
+  MMVM_CK(grow(c->msum, K * n));
+  MMVM_CK(grow(c->rdx, 2 * n));
+  MMVM_CK(grow(c->rdm, K * n));
+  if (n > 1) {
+    c->chunks = choose_chunks(c, n);
+    MMVM_CK(grow(c->rec, (size_t)n * c->pe.rec_len * c->pe.elem_bytes));
+    MMVM_CK(grow(c->partial, (size_t)c->chunks * c->NB * n));
+  } else {
+    c->chunks = 0;
+  }
+  if (realloc) c->drop_graph();
+  return MMVM_OK;
+}
+
+// One RHS evaluation: mode 0 writes (rdx, rdm); modes 1..4 are RK4 stages.
+int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, double cs,
+                const double* dt_dev) {
+  const int n = (int)c->n;
+  const double lam0sq = c->cfg.lambda0 * c->cfg.lambda0;
+  const double four_nu = 4.0 * c->cfg.nu;
+  if (n > 1) {
+    MMVM_CK(mmvm::launch_prep(c->cfg.precision, n, c->M, xin, min_, c->t_dev(), dt_dev, cs,
+                              lam0sq, four_nu, c->rec.p, c->st));
+    MMVM_CK(c->pe.launch(c->rec.p, n, c->chunks, c->S, c->partial.p, c->st));
+    c->launches += 2;
+  }
+  mmvm::FinishArgs A;
+  A.n = n;
+  A.M = c->M;
+  A.K = c->K;
+  A.NB = c->NB;
+  A.nchunks = n > 1 ? c->chunks : 0;
+  A.targets_per_block = c->finish_tb;
+  A.partial = n > 1 ? c->partial.p : nullptr;
+  A.Min = min_;
+  A.k_off = c->k_off.p;
+  A.e_l = c->e_l.p;
+  A.e_b = c->e_b.p;
+  A.e_c = c->e_c.p;
+  A.psi0 = c->psi0.p;
+  A.lam0sq = lam0sq;
+  A.four_nu = four_nu;
+  A.t_dev = c->t_dev();
+  A.dt_dev = dt_dev;
+  A.cs = cs;
+  A.mode = mode;
+  A.out_dx = c->rdx.p;
+  A.out_dM = c->rdm.p;
+  A.y_x = c->x.p;
+  A.y_M = c->m.p;
+  A.ys_x = c->xs.p;
+  A.ys_M = c->ms.p;
+  A.sum_x = c->xsum.p;
+  A.sum_M = c->msum.p;
+  MMVM_CK(mmvm::launch_finish(A, c->st));
+  c->launches += 1;
+  return MMVM_OK;
+}
+
+int enqueue_step(mmvm_ctx* c) {
+  int rc;
+  double* dt = c->dt_dev();
+  if ((rc = enqueue_rhs(c, 1, c->x.p, c->m.p, 0.0, dt))) return rc;
+  if ((rc = enqueue_rhs(c, 2, c->xs.p, c->ms.p, 0.5, dt))) return rc;
+  if ((rc = enqueue_rhs(c, 3, c->xs.p, c->ms.p, 0.5, dt))) return rc;
+  if ((rc = enqueue_rhs(c, 4, c->xs.p, c->ms.p, 1.0, dt))) return rc;
+  MMVM_CK(mmvm::launch_advance_time(c->t_dev(), dt, c->st));
+  c->launches += 1;
+  return MMVM_OK;
+}
+
+int check_host_state(const mmvm_ctx* c, int64_t n, const double* x, const double* mom) {
+  for (int64_t j = 0; j < n; ++j) {
+    if (!std::isfinite(x[2 * j]) || !std::isfinite(x[2 * j + 1]))
+      return fail(MMVM_E_NUMERIC, "non-finite position at particle " + std::to_string(j));
+    for (int k = 0; k < c->K; ++k)
+      if (!std::isfinite(mom[j * c->K + k]))
+        return fail(MMVM_E_NUMERIC, "non-finite moment at particle " + std::to_string(j));
+    if (mom[j * c->K] == 0.0)
+      return fail(MMVM_E_ZERO_CIRCULATION,
+                  "M[0,0] == 0 at particle " + std::to_string(j) + " (eq:mass)");
+  }
+  return MMVM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mmvm_last_error(void) { return g_err.c_str(); }
+
+int32_t mmvm_num_moments(int32_t order) { return order < 0 ? 0 : mmvm::n_moments(order); }
+
+int64_t mmvm_num_particles(const mmvm_ctx* c) { return c ? c->n : 0; }
+
+int64_t mmvm_launch_count(const mmvm_ctx* c) { return c ? c->launches : 0; }
+
+int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
+  g_err.clear();
+  if (!cfg || !out) return fail(MMVM_E_INVALID_ARG, "null config or output handle");
+  *out = nullptr;
+  if (cfg->order < 0) return fail(MMVM_E_INVALID_ARG, "order must be >= 0");
+  if (cfg->order > MMVM_MAX_ORDER_SINGLE)
+    return fail(MMVM_E_UNSUPPORTED, "order above MMVM_MAX_ORDER_SINGLE");
+  if (cfg->precision != MMVM_FP64 && cfg->precision != MMVM_MIXED_FP32)
+    return fail(MMVM_E_INVALID_ARG, "unknown precision");
+  if (!(cfg->lambda0 > 0.0) || !std::isfinite(cfg->lambda0))
+    return fail(MMVM_E_INVALID_ARG, "lambda0 must be positive and finite");
+  if (!(cfg->nu >= 0.0) || !std::isfinite(cfg->nu))
+    return fail(MMVM_E_INVALID_ARG, "nu must be >= 0 and finite");
+  if (cfg->flags != 0) return fail(MMVM_E_INVALID_ARG, "flags must be 0");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (cfg->device < 0 || cfg->device >= ndev)
+    return fail(MMVM_E_INVALID_ARG, "device ordinal out of range");
+  e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+
+  mmvm_ctx* c = new mmvm_ctx();
+  c->cfg = *cfg;
+  c->M = cfg->order;
+  c->K = mmvm::n_moments(c->M);
+  c->NB = mmvm::n_beta(c->M);
+  if (c->M <= MMVM_MAX_ORDER_PAIRS) {
+    c->pe = mmvm::pair_entry(c->M, cfg->precision);
+    if (c->pe.M != c->M) {
+      delete c;
+      return fail(MMVM_E_UNSUPPORTED, "pair kernel variant not compiled");
+    }
+  }
+  const int K = c->K;
+  c->finish_tb = std::max(1, 128 / (((K + 31) / 32) * 32));
+  auto bail = [&](int rc) {
+    mmvm_destroy(c);
+    return rc;
+  };
+  if ((e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail(e, "cudaStreamCreate"));
+  c->st = c->own;
+  mmvm::FinishTables T = mmvm::build_finish_tables(c->M);
+  if ((e = c->k_off.ensure(T.k_off.size())) != cudaSuccess ||
+      (e = c->e_l.ensure(T.e_l.size())) != cudaSuccess ||
+      (e = c->e_b.ensure(T.e_b.size())) != cudaSuccess ||
+      (e = c->e_c.ensure(T.e_c.size())) != cudaSuccess ||
+      (e = c->psi0.ensure(T.psi0.size())) != cudaSuccess ||
+      (e = c->scal.ensure(2)) != cudaSuccess || (e = c->flags.ensure(2)) != cudaSuccess)
+    return bail(cuda_fail(e, "cudaMalloc(tables)"));
+  auto up = [&](void* d, const void* h, size_t bytes) {
+    return bytes ? cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  if ((e = up(c->k_off.p, T.k_off.data(), T.k_off.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(c->e_l.p, T.e_l.data(), T.e_l.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(c->e_b.p, T.e_b.data(), T.e_b.size() * sizeof(int))) != cudaSuccess ||
+      (e = up(c->e_c.p, T.e_c.data(), T.e_c.size() * sizeof(double))) != cudaSuccess ||
+      (e = up(c->psi0.p, T.psi0.data(), T.psi0.size() * sizeof(double))) != cudaSuccess ||
+      (e = cudaMemset(c->scal.p, 0, 2 * sizeof(double))) != cudaSuccess)
+    return bail(cuda_fail(e, "cudaMemcpy(tables)"));
+  if (c->pe.prepare && (e = c->pe.prepare(c->S)) != cudaSuccess)
+    return bail(cuda_fail(e, "pair kernel shared-memory limit"));
+  *out = c;
+  return MMVM_OK;
+}
+
+void mmvm_destroy(mmvm_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->cfg.device);
+  if (c->st) cudaStreamSynchronize(c->st);
+  c->drop_graph();
+  for (auto* b : {&c->x, &c->m, &c->xs, &c->ms, &c->xsum, &c->msum, &c->rdx, &c->rdm, &c->scal,
+                  &c->partial, &c->e_c, &c->psi0})
+    b->release();
+  c->rec.release();
+  c->flags.release();
+  c->k_off.release();
+  c->e_l.release();
+  c->e_b.release();
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+}
+
+int mmvm_set_stream(mmvm_ctx* c, void* stream) {
+  if (!c) return fail(MMVM_E_INVALID_ARG, "null context");
+  c->st = stream ? (cudaStream_t)stream : c->own;
+  c->drop_graph();
+  return MMVM_OK;
+}
+
+int mmvm_synchronize(mmvm_ctx* c) {
+  if (!c) return fail(MMVM_E_INVALID_ARG, "null context");
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  return MMVM_OK;
+}
+
+static int set_state_common(mmvm_ctx* c, int64_t n, const double* x, const double* mom,
+                            double t, cudaMemcpyKind kind) {
+  if (!c || !x || !mom) return fail(MMVM_E_INVALID_ARG, "null argument");
+  if (n < 1 || n > (int64_t)1 << 30) return fail(MMVM_E_INVALID_ARG, "n out of range");
+  if (!std::isfinite(t)) return fail(MMVM_E_INVALID_ARG, "t must be finite");
+  if (n > 1 && c->M > MMVM_MAX_ORDER_PAIRS)
+    return fail(MMVM_E_UNSUPPORTED, "order above MMVM_MAX_ORDER_PAIRS for n > 1");
+  if (c->cfg.lambda0 * c->cfg.lambda0 + 4.0 * c->cfg.nu * t <= 0.0)
+    return fail(MMVM_E_INVALID_ARG, "lambda(t)^2 <= 0");
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  if (kind == cudaMemcpyHostToDevice) {
+    int rc = check_host_state(c, n, x, mom);
+    if (rc) return rc;
+  }
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  c->n = n;
+  int rc = ensure_buffers(c, n);
+  if (rc) return rc;
+  MMVM_CK(cudaMemcpyAsync(c->x.p, x, sizeof(double) * 2 * n, kind, c->st));
+  MMVM_CK(cudaMemcpyAsync(c->m.p, mom, sizeof(double) * c->K * n, kind, c->st));
+  static thread_local double t_host;
+  t_host = t;
+  MMVM_CK(cudaMemcpyAsync(c->t_dev(), &t_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  return MMVM_OK;
+}
+
+int mmvm_set_state(mmvm_ctx* c, int64_t n, const double* x, const double* mom, double t) {
+  g_err.clear();
+  return set_state_common(c, n, x, mom, t, cudaMemcpyHostToDevice);
+}
+
+int mmvm_set_state_device(mmvm_ctx* c, int64_t n, const double* x, const double* mom,
+                          double t) {
+  g_err.clear();
+  return set_state_common(c, n, x, mom, t, cudaMemcpyDeviceToDevice);
+}
+
+int mmvm_get_state(mmvm_ctx* c, double* x, double* mom, double* t) {
+  if (!c) return fail(MMVM_E_INVALID_ARG, "null context");
+  if (c->n < 1) return fail(MMVM_E_INVALID_ARG, "no state loaded");
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  if (x) MMVM_CK(cudaMemcpyAsync(x, c->x.p, sizeof(double) * 2 * c->n, cudaMemcpyDeviceToHost, c->st));
+  if (mom)
+    MMVM_CK(cudaMemcpyAsync(mom, c->m.p, sizeof(double) * c->K * c->n, cudaMemcpyDeviceToHost, c->st));
+  if (t) MMVM_CK(cudaMemcpyAsync(t, c->t_dev(), sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  return MMVM_OK;
+}
+
+int mmvm_get_state_device(mmvm_ctx* c, double* d_x, double* d_mom) {
+  if (!c || !d_x || !d_mom) return fail(MMVM_E_INVALID_ARG, "null argument");
+  if (c->n < 1) return fail(MMVM_E_INVALID_ARG, "no state loaded");
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  MMVM_CK(cudaMemcpyAsync(d_x, c->x.p, sizeof(double) * 2 * c->n, cudaMemcpyDeviceToDevice, c->st));
+  MMVM_CK(cudaMemcpyAsync(d_mom, c->m.p, sizeof(double) * c->K * c->n, cudaMemcpyDeviceToDevice, c->st));
+  return MMVM_OK;
+}
+
+int mmvm_rhs_device(mmvm_ctx* c, double* d_dx, double* d_dM) {
+  if (!c || !d_dx || !d_dM) return fail(MMVM_E_INVALID_ARG, "null argument");
+  if (c->n < 1) return fail(MMVM_E_INVALID_ARG, "no state loaded");
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  int rc = enqueue_rhs(c, 0, c->x.p, c->m.p, 0.0, nullptr);
+  if (rc) return rc;
+  MMVM_CK(cudaMemcpyAsync(d_dx, c->rdx.p, sizeof(double) * 2 * c->n, cudaMemcpyDeviceToDevice, c->st));
+  MMVM_CK(cudaMemcpyAsync(d_dM, c->rdm.p, sizeof(double) * c->K * c->n, cudaMemcpyDeviceToDevice, c->st));
+  return MMVM_OK;
+}
+
+int mmvm_rhs(mmvm_ctx* c, double* dx, double* dM) {
+  if (!c || !dx || !dM) return fail(MMVM_E_INVALID_ARG, "null argument");
+  if (c->n < 1) return fail(MMVM_E_INVALID_ARG, "no state loaded");
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  int rc = enqueue_rhs(c, 0, c->x.p, c->m.p, 0.0, nullptr);
+  if (rc) return rc;
+  MMVM_CK(cudaMemcpyAsync(dx, c->rdx.p, sizeof(double) * 2 * c->n, cudaMemcpyDeviceToHost, c->st));
+  MMVM_CK(cudaMemcpyAsync(dM, c->rdm.p, sizeof(double) * c->K * c->n, cudaMemcpyDeviceToHost, c->st));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  return MMVM_OK;
+}
+
+int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
+  if (!c) return fail(MMVM_E_INVALID_ARG, "null context");
+  if (c->n < 1) return fail(MMVM_E_INVALID_ARG, "no state loaded");
+  if (!std::isfinite(dt) || nsteps < 0) return fail(MMVM_E_INVALID_ARG, "bad dt or nsteps");
+  if (nsteps == 0) return MMVM_OK;
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  static thread_local double dt_host;
+  dt_host = dt;
+  MMVM_CK(cudaMemcpyAsync(c->dt_dev(), &dt_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  if (!c->graph_ok) {
+    MMVM_CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = c->launches;
+    int rc = enqueue_step(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    c->launches = before;  // captured launches are counted on replay
+    c->graph = g;
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (e != cudaSuccess) {
+      c->drop_graph();
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    c->graph_ok = true;
+  }
+  const int per_step = (c->n > 1 ? 12 : 4) + 1;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    MMVM_CK(cudaGraphLaunch(c->gexec, c->st));
+    c->launches += per_step;
+  }
+  return MMVM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Shared compile-time index helpers and small device utilities of the MMVM
+// kernels.  Index conventions (c = 2 lambda^2, zeta = x / sqrt(c)):
+//  * moment column of (k1, k2):  mcol = q(k1+k2) + k2, q(s) = s(s+1)/2;
+//  * stream-function correlation Psi[beta] for 1 <= |beta| <= BMAX, column
+//    bcol = q(b1+b2) + b2 - 1 (beta = 0 is never needed);
+//  * BMAX = 2M covers the velocity jet W[gamma], |gamma| <= 2M-1, that the
+//    moment equations need (eq:FinalCrossI/II) and the |m| <= M entries of
+//    the centroid equation (eq:xjdot_Final); for M = 0 it is 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+namespace mmvm {
+
+__host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
+__host__ __device__ constexpr int n_moments(int M) { return tri(M + 1); }
+__host__ __device__ constexpr int mcol(int k1, int k2) { return tri(k1 + k2) + k2; }
+__host__ __device__ constexpr int bmax_of(int M) { return M == 0 ? 1 : 2 * M; }
+__host__ __device__ constexpr int n_beta(int M) { return tri(bmax_of(M) + 1) - 1; }
+__host__ __device__ constexpr int bcol(int b1, int b2) { return tri(b1 + b2) + b2 - 1; }
+// Highest order of the stream-function jet a pair needs: |m + beta| <= M + BMAX.
+__host__ __device__ constexpr int jet_order(int M) { return M + bmax_of(M); }
+
+__host__ __device__ constexpr double binom_d(int n, int k) {
+  double r = 1.0;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+__host__ __device__ constexpr double pow2_neg(int n) {
+  double r = 1.0;
+  for (int i = 0; i < n; ++i) r *= 0.5;
+  return r;
+}
+
+// Source record: FP32 mode stores zeta split into (hi, lo) floats so that
+// differences of nearby centres are exact; FP64 stores zeta directly.
+template <typename T> struct Rec;
+template <> struct Rec<float> {
+  static constexpr int HDR = 4;  // zh1, zh2, zl1, zl2
+};
+template <> struct Rec<double> {
+  static constexpr int HDR = 2;  // z1, z2
+};
+__host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+template <typename T>
+__host__ __device__ constexpr int rec_len(int M) {
+  // pad to 16 bytes so a record (and a tile of records) can be bulk-copied
+  return round_up(Rec<T>::HDR + n_moments(M), 16 / (int)sizeof(T));
+}
+
+// Compile-time loop: f(std::integral_constant<int, i>) for i in [B, E).
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+// Descending: i = E-1 down to B.
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for_down(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, E - 1>{});
+    static_for_down<B, E - 1>(f);
+  }
+}
+
+__device__ __forceinline__ float dexp(float v) { return expf(v); }
+__device__ __forceinline__ double dexp(double v) { return exp(v); }
+
+}  // namespace mmvm

@@ -1,0 +1,199 @@
+// All-pairs interaction kernel of the MMVM cross term (Appendix A.2).
+//
+// For a target j and a source j' the moment equations need the velocity jet
+// of the source's Gaussian of core sqrt(2) lambda at the separation
+// s = x^j - x^{j'} (eq:Fullint with b = s, eq:FinalCrossI/II), contracted with
+// the source moments:  W_c[gamma] = sum_m M^{j'}_m D^{m+gamma} V_00,c(s; sqrt2 lambda).
+// V_00 = grad-perp psi with the stream function psi of that Gaussian, so both
+// components follow from one scalar correlation
+//     Psi[beta] = sum_m a_m D^{m+beta} psi(b),   1 <= |beta| <= BMAX,
+//     W_1[gamma] = -Psi[gamma + e2],  W_2[gamma] = Psi[gamma + e1],
+// in units where c = 2 lambda^2 = 1: b = s / sqrt(c), a_m = M_m c^{-|m|/2}
+// (the finish kernel undoes the scaling).  Per pair this kernel builds the
+// Cartesian jet D^alpha psi(b), 1 <= |alpha| <= NJ = M + BMAX, one order at a
+// time and adds each order into the K x |beta| correlation before the next
+// order is formed, so only one order of the jet is live in registers.
+//
+// Jet of one order n (derivation in the design notes; every step is exact):
+//  * psi is radial, psi = Psi(|b|^2) with Psi' = (1 - e^{-x})/(4 pi x), so the
+//    holomorphic edge is  d^n psi / dz^n = (1/4pi) (-1)^{n-1} zbar^n I_{n-1}(x),
+//    I_k(x) = int_0^1 t^k e^{-xt} dt (x = |b|^2, z = b1 + i b2);
+//  * Lap psi = e^{-x}/pi, whose Cartesian jet e_(a,b) = h_a(b1) h_b(b2) is a
+//    product of Hermite functions h_k(t) = d^k/dt^k e^{-t^2} (1/pi folded in);
+//  * with c_a = D_1^a D_2^{n-a} psi the Laplacian gives c_{a+2} = e_(a,n-2-a) - c_a,
+//    i.e. c_a = (-1)^{floor(a/2)} c_{a mod 2} + chi_a with chi_0 = chi_1 = 0,
+//    chi_{a+2} = e_(a,n-2-a) - chi_a;
+//  * expanding d/dz = (D_1 - i D_2)/2 then fixes the two seeds:
+//    c_0 + i c_1 = 2 i^n [ d^n psi/dz^n - 2^{-n} sum_a C(n,a) (-i)^{n-a} chi_a ].
+// I_k is formed by the upward recurrence I_k = (k I_{k-1} - e^{-x})/x where it
+// is stable (k <= x) and downward from a Kummer series at the top order
+// otherwise; for x >= 40 the edge zbar^n I_{n-1} itself is run upward in
+// complex arithmetic so that nothing under- or overflows at large |b|.
+#pragma once
+
+#include "common.cuh"
+
+namespace mmvm {
+
+constexpr double kInvPi = 0.31830988618379067154;
+constexpr double kInv4Pi = 0.07957747154594766788;
+
+template <typename T> __device__ __forceinline__ T rcp(T v);
+template <> __device__ __forceinline__ float rcp<float>(float v) { return __frcp_rn(v); }
+template <> __device__ __forceinline__ double rcp<double>(double v) { return 1.0 / v; }
+
+// sum_{k>=0} x^k / ((P+1)(P+2)...(P+k+1)) so that I_P(x) = e^{-x} * sum (x < P).
+template <int P, typename T>
+__device__ __forceinline__ T kummer_sum(T x) {
+  constexpr bool f32 = std::is_same<T, float>::value;
+  const T eps = f32 ? T(2e-8) : T(5e-18);
+  constexpr int kmax = f32 ? 48 : 80;
+  T term = T(1.0 / (P + 1));
+  T s = term;
+#pragma unroll 1
+  for (int k = 1; k < kmax; ++k) {
+    term = term * x * rcp<T>(T(P + 1 + k));
+    s += term;
+    if (term <= eps * s) break;
+  }
+  return s;
+}
+
+template <int M, typename T, int G, int g>
+struct PairNear {
+  static constexpr int K = n_moments(M);
+  static constexpr int NB = n_beta(M);
+  static constexpr int NJ = jet_order(M);
+  static constexpr int BMAX = bmax_of(M);
+  static constexpr int B0 = g * NB / G;
+  static constexpr int B1 = (g + 1) * NB / G;
+  static constexpr int NBL = B1 - B0;
+  static constexpr int HN = NJ >= 2 ? NJ - 1 : 1;  // Hermite functions h_0..h_{NJ-2}
+
+  // Add one source's contribution (moments a[K], separation b in c = 1 units)
+  // to my slice acc[NBL] of Psi.  wmask = 0 removes the pair exactly (it is
+  // used for the self pair, whose separation the caller moves far away).
+  __device__ __forceinline__ static void run(T b1, T b2, T wmask, const T (&a)[K],
+                                             T (&acc)[NBL]) {
+    const T x = b1 * b1 + b2 * b2;
+    const T ex1 = dexp(-b1 * b1);
+    const T ex2 = dexp(-b2 * b2);
+    const T E = ex1 * ex2;
+    // w[n-1] = zbar^n I_{n-1}(x), n = 1..NJ
+    T wr[NJ], wi[NJ];
+    if (x < T(40)) {
+      constexpr int P = NJ - 1;
+      T I[P + 1];
+      const T rx = T(1) / x;  // inf at x == 0: those entries are replaced below
+      I[0] = (T(1) - E) * rx;
+      static_for<1, P + 1>([&](auto nc) {
+        constexpr int k = decltype(nc)::value;
+        I[k] = (T(k) * I[k - 1] - E) * rx;
+      });
+      if (x < T(P) || x < T(1)) {
+        T Id = E * kummer_sum<P, T>(x);
+        static_for_down<1, P + 1>([&](auto nc) {
+          constexpr int k = decltype(nc)::value;
+          if (T(k) > x) I[k] = Id;
+          Id = (x * Id + E) * T(1.0 / k);
+        });
+        if (x < T(1)) I[0] = Id;
+      }
+      T zr = b1, zi = -b2;
+      static_for<0, NJ>([&](auto nc) {
+        constexpr int k = decltype(nc)::value;
+        if constexpr (k > 0) {
+          const T tr = zr * b1 + zi * b2;
+          const T ti = zi * b1 - zr * b2;
+          zr = tr;
+          zi = ti;
+        }
+        wr[k] = zr * I[k];
+        wi[k] = zi * I[k];
+      });
+    } else {
+      const T rx = T(1) / x;
+      T qr = E * b1, qi = -E * b2;  // E zbar^{n}
+      const T f0 = (T(1) - E) * rx;
+      wr[0] = b1 * f0;
+      wi[0] = -b2 * f0;
+      static_for<1, NJ>([&](auto nc) {
+        constexpr int k = decltype(nc)::value;  // order k+1 from order k
+        const T tr = qr * b1 + qi * b2;
+        const T ti = qi * b1 - qr * b2;
+        qr = tr;
+        qi = ti;
+        const T pr = wr[k - 1] * b1 + wi[k - 1] * b2;
+        const T pi = wi[k - 1] * b1 - wr[k - 1] * b2;
+        wr[k] = (T(k) * pr - qr) * rx;
+        wi[k] = (T(k) * pi - qi) * rx;
+      });
+    }
+    // Hermite functions: hx[k] = h_k(b1)/pi, hy[k] = h_k(b2)
+    T hx[HN], hy[HN];
+    hx[0] = ex1 * T(kInvPi);
+    hy[0] = ex2;
+    if constexpr (HN > 1) {
+      hx[1] = T(-2) * b1 * hx[0];
+      hy[1] = T(-2) * b2 * hy[0];
+    }
+    static_for<1, HN - 1>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      hx[k + 1] = T(-2) * b1 * hx[k] - T(2 * k) * hx[k - 1];
+      hy[k + 1] = T(-2) * b2 * hy[k] - T(2 * k) * hy[k - 1];
+    });
+
+    static_for<1, NJ + 1>([&](auto nc) {
+      constexpr int n = decltype(nc)::value;
+      const T f = T(((n - 1) & 1) ? -kInv4Pi : kInv4Pi) * wmask;
+      const T w_r = wr[n - 1] * f;
+      const T w_i = wi[n - 1] * f;
+      T chi[n + 1];
+      chi[0] = T(0);
+      chi[1] = T(0);
+      T pr = T(0), pi = T(0);
+      static_for<2, n + 1>([&](auto ac) {
+        constexpr int aa = decltype(ac)::value;
+        chi[aa] = hx[aa - 2] * hy[n - aa] - chi[aa - 2];
+        constexpr T wgt = T(binom_d(n, aa) * pow2_neg(n));
+        constexpr int r = (n - aa) & 3;  // (-i)^r
+        if constexpr (r == 0) pr += wgt * chi[aa];
+        if constexpr (r == 1) pi -= wgt * chi[aa];
+        if constexpr (r == 2) pr -= wgt * chi[aa];
+        if constexpr (r == 3) pi += wgt * chi[aa];
+      });
+      const T dr = w_r - pr;
+      const T di = w_i - pi;
+      T c0, c1;  // 2 i^n (dr + i di)
+      if constexpr ((n & 3) == 0) { c0 = T(2) * dr;  c1 = T(2) * di; }
+      if constexpr ((n & 3) == 1) { c0 = T(-2) * di; c1 = T(2) * dr; }
+      if constexpr ((n & 3) == 2) { c0 = T(-2) * dr; c1 = T(-2) * di; }
+      if constexpr ((n & 3) == 3) { c0 = T(2) * di;  c1 = T(-2) * dr; }
+      static_for<0, n + 1>([&](auto ac) {
+        constexpr int aa = decltype(ac)::value;
+        constexpr T s = ((aa >> 1) & 1) ? T(-1) : T(1);
+        T ca;
+        if constexpr (aa < 2) ca = s * ((aa & 1) ? c1 : c0);
+        else ca = s * ((aa & 1) ? c1 : c0) + chi[aa];
+        // alpha = (aa, n - aa);  beta = alpha - m for every moment m <= alpha
+        static_for<0, M + 1>([&](auto m1c) {
+          constexpr int m1 = decltype(m1c)::value;
+          static_for<0, M - m1 + 1>([&](auto m2c) {
+            constexpr int m2 = decltype(m2c)::value;
+            constexpr int bb1 = aa - m1;
+            constexpr int bb2 = n - aa - m2;
+            constexpr int bn = bb1 + bb2;
+            if constexpr (bb1 >= 0 && bb2 >= 0 && bn >= 1 && bn <= BMAX) {
+              constexpr int col = bcol(bb1, bb2);
+              if constexpr (col >= B0 && col < B1) {
+                acc[col - B0] += a[mcol(m1, m2)] * ca;
+              }
+            }
+          });
+        });
+      });
+    });
+  }
+};
+
+}  // namespace mmvm

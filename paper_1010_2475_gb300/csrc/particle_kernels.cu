@@ -1,0 +1,230 @@
+// Per-particle kernels of the MMVM right-hand side (FP64):
+//  * prep:   core spreading lambda(t)^2 = lambda_0^2 + 4 nu t (eq:phi00) at the
+//            stage time, c = 2 lambda^2, and the source records
+//            (zeta = x / sqrt(c), a_m = M_m c^{-|m|/2}) for the pair kernel;
+//  * finish: sum of the pair partials over source chunks, the self pair from
+//            the jet at the origin, the centroid velocity (eq:xjdot_Final, self
+//            pair excluded), the moment equation (eq:Final_CrossCoef with the
+//            (i,q) sums of eq:FinalSingleI/II folded into tables) including the
+//            transport term C (eq:last_termsimp), and optionally the classic
+//            RK4 stage combination;
+//  * advance_time: t += dt after the fourth stage.
+#include "particle_kernels.h"
+
+#include "common.cuh"
+
+namespace mmvm {
+
+__device__ __forceinline__ double stage_c(const double* t_dev, const double* dt_dev,
+                                          double cs, double lam0sq, double four_nu) {
+  const double t = *t_dev + cs * (dt_dev ? *dt_dev : 0.0);
+  return 2.0 * (lam0sq + four_nu * t);
+}
+
+template <typename T>
+__global__ void prep_kernel(int n, int M, int K, int R, const double* __restrict__ x,
+                            const double* __restrict__ mom, const double* t_dev,
+                            const double* dt_dev, double cs, double lam0sq, double four_nu,
+                            T* __restrict__ rec) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double c = stage_c(t_dev, dt_dev, cs, lam0sq, four_nu);
+  const double irc = 1.0 / sqrt(c);
+  T* r = rec + (size_t)j * R;
+  const double z1 = x[2 * j] * irc;
+  const double z2 = x[2 * j + 1] * irc;
+  int h;
+  if constexpr (sizeof(T) == 4) {
+    const float h1 = (float)z1, h2 = (float)z2;
+    r[0] = h1;
+    r[1] = h2;
+    r[2] = (float)(z1 - (double)h1);
+    r[3] = (float)(z2 - (double)h2);
+    h = 4;
+  } else {
+    r[0] = (T)z1;
+    r[1] = (T)z2;
+    h = 2;
+  }
+  const double* mj = mom + (size_t)j * K;
+  double sc = 1.0;
+  int col = 0;
+  for (int s = 0; s <= M; ++s) {
+    for (int k2 = 0; k2 <= s; ++k2, ++col) r[h + col] = (T)(mj[col] * sc);
+    sc *= irc;
+  }
+  for (int p = h + K; p < R; ++p) r[p] = T(0);
+}
+
+// Shared-memory layout per block: for each of TB targets, Psi[NB], a[K], X[2],
+// M_00 (read before any in-place stage write), then the powers c^{-s/2}.
+__global__ void finish_kernel(FinishArgs A) {
+  extern __shared__ double sm[];
+  const int TB = A.targets_per_block;
+  const int NB = A.NB, K = A.K, M = A.M;
+  double* psi = sm;                       // TB * NB
+  double* at = psi + TB * NB;             // TB * K
+  double* X = at + TB * K;                // TB * 2
+  double* m00s = X + TB * 2;              // TB
+  double* cpow = m00s + TB;               // c^{-s/2}, s = 0..2M+2
+  const int j0 = blockIdx.x * TB;
+  const double c = stage_c(A.t_dev, A.dt_dev, A.cs, A.lam0sq, A.four_nu);
+  for (int s = threadIdx.x; s <= 2 * M + 2; s += blockDim.x) cpow[s] = pow(c, -0.5 * s);
+  __syncthreads();
+  // 1. Psi_excl = sum over source chunks (fixed order), scaled moments
+  for (int idx = threadIdx.x; idx < TB * NB; idx += blockDim.x) {
+    const int tt = idx / NB, b = idx % NB, j = j0 + tt;
+    double v = 0.0;
+    if (j < A.n && A.partial) {
+      for (int ch = 0; ch < A.nchunks; ++ch) v += A.partial[((size_t)ch * NB + b) * A.n + j];
+    }
+    psi[idx] = v;
+  }
+  for (int idx = threadIdx.x; idx < TB * K; idx += blockDim.x) {
+    const int tt = idx / K, m = idx % K, j = j0 + tt;
+    int s = 0;
+    while ((s + 1) * (s + 2) / 2 <= m) ++s;  // total order of column m
+    const double mv = (j < A.n) ? A.Min[(size_t)j * K + m] : 0.0;
+    at[idx] = mv * cpow[s];
+    if (m == 0) m00s[tt] = (j < A.n) ? mv : 1.0;
+  }
+  __syncthreads();
+  // 2. centroid sums X_c = sum_m (-1)^{|m|} a_m What_c[m], What_1[m] = -Psi[m+e2],
+  //    What_2[m] = Psi[m+e1]  (eq:xjdot_Final in c = 1 units, self pair excluded)
+  for (int idx = threadIdx.x; idx < TB * 2; idx += blockDim.x) {
+    const int tt = idx >> 1, comp = idx & 1;
+    double acc = 0.0;
+    int col = 0;
+    for (int s = 0; s <= M; ++s) {
+      const double sg = (s & 1) ? -1.0 : 1.0;
+      for (int m2 = 0; m2 <= s; ++m2, ++col) {
+        const int m1 = s - m2;
+        const double a = at[tt * K + col];
+        if (comp == 0) acc -= sg * a * psi[tt * NB + bcol(m1, m2 + 1)];
+        else acc += sg * a * psi[tt * NB + bcol(m1 + 1, m2)];
+      }
+    }
+    X[idx] = acc;
+  }
+  __syncthreads();
+  // 3. add the self pair: Psi_self[beta] = sum_m a_m psi0[m + beta]
+  for (int idx = threadIdx.x; idx < TB * NB; idx += blockDim.x) {
+    const int tt = idx / NB, b = idx % NB;
+    int bn = 1;
+    while (tri(bn + 1) - 1 <= b) ++bn;
+    const int b2 = b + 1 - tri(bn), b1 = bn - b2;
+    double acc = 0.0;
+    int col = 0;
+    for (int s = 0; s <= M; ++s) {
+      for (int m2 = 0; m2 <= s; ++m2, ++col) {
+        const int a1 = s - m2 + b1, a2 = m2 + b2;
+        if ((a1 | a2) & 1) continue;  // psi0 vanishes at odd indices
+        acc += at[tt * K + col] * A.psi0[tri(a1 + a2) + a2];
+      }
+    }
+    psi[idx] += acc;
+  }
+  __syncthreads();
+  // 4. moment equation and centroid velocity per (target, k)
+  for (int idx = threadIdx.x; idx < TB * K; idx += blockDim.x) {
+    const int tt = idx / K, k = idx % K, j = j0 + tt;
+    if (j >= A.n) continue;
+    int kn = 0;
+    while ((kn + 1) * (kn + 2) / 2 <= k) ++kn;
+    const int k2 = k - tri(kn), k1 = kn - k2;
+    const double* a = at + tt * K;
+    const double* ps = psi + tt * NB;
+    double R = 0.0;
+    for (int e = A.k_off[k]; e < A.k_off[k + 1]; ++e) R += A.e_c[e] * a[A.e_l[e]] * ps[A.e_b[e]];
+    const double m00 = m00s[tt];
+    double ctr = 0.0;
+    if (k1 >= 1) ctr += X[2 * tt] * a[mcol(k1 - 1, k2)];
+    if (k2 >= 1) ctr += X[2 * tt + 1] * a[mcol(k1, k2 - 1)];
+    const double dm = (R + ctr / m00) / (cpow[kn] * c);  // c^{|k|/2 - 1}
+    const size_t o = (size_t)j * K + k;
+    if (A.mode == 0) {
+      A.out_dM[o] = dm;
+    } else {
+      const double h = *A.dt_dev;
+      const double base = A.y_M[o];
+      if (A.mode == 1) { A.ys_M[o] = base + 0.5 * h * dm; A.sum_M[o] = base + h / 6.0 * dm; }
+      if (A.mode == 2) { A.ys_M[o] = base + 0.5 * h * dm; A.sum_M[o] += h / 3.0 * dm; }
+      if (A.mode == 3) { A.ys_M[o] = base + h * dm;       A.sum_M[o] += h / 3.0 * dm; }
+      if (A.mode == 4) { A.y_M[o] = A.sum_M[o] + h / 6.0 * dm; }
+    }
+  }
+  // 5. centroid velocity xdot_c = c^{-1/2} X_c / M_00 and its stage update
+  for (int idx = threadIdx.x; idx < TB * 2; idx += blockDim.x) {
+    const int tt = idx >> 1, comp = idx & 1, j = j0 + tt;
+    if (j >= A.n) continue;
+    const double dx = X[idx] * cpow[1] / m00s[tt];
+    const size_t ox = (size_t)j * 2 + comp;
+    if (A.mode == 0) {
+      A.out_dx[ox] = dx;
+    } else {
+      const double h = *A.dt_dev;
+      const double base = A.y_x[ox];
+      if (A.mode == 1) { A.ys_x[ox] = base + 0.5 * h * dx; A.sum_x[ox] = base + h / 6.0 * dx; }
+      if (A.mode == 2) { A.ys_x[ox] = base + 0.5 * h * dx; A.sum_x[ox] += h / 3.0 * dx; }
+      if (A.mode == 3) { A.ys_x[ox] = base + h * dx;       A.sum_x[ox] += h / 3.0 * dx; }
+      if (A.mode == 4) { A.y_x[ox] = A.sum_x[ox] + h / 6.0 * dx; }
+    }
+  }
+}
+
+__global__ void advance_time_kernel(double* t_dev, const double* dt_dev) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *t_dev += *dt_dev;
+}
+
+// Non-finite / zero-circulation scan of a state (flags[0]: non-finite,
+// flags[1]: zero circulation); used after set_state and on demand.
+__global__ void scan_state_kernel(int n, int K, const double* __restrict__ x,
+                                  const double* __restrict__ mom, int* flags) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  bool bad = !isfinite(x[2 * j]) || !isfinite(x[2 * j + 1]);
+  for (int m = 0; m < K; ++m) bad |= !isfinite(mom[(size_t)j * K + m]);
+  if (bad) atomicOr(flags, 1);
+  if (mom[(size_t)j * K] == 0.0) atomicOr(flags + 1, 1);
+}
+
+cudaError_t launch_prep(int precision, int n, int M, const double* x, const double* mom,
+                        const double* t_dev, const double* dt_dev, double cs, double lam0sq,
+                        double four_nu, void* rec, cudaStream_t st) {
+  const int K = n_moments(M);
+  const int threads = 128, blocks = (n + threads - 1) / threads;
+  if (precision == 1) {
+    prep_kernel<float><<<blocks, threads, 0, st>>>(n, M, K, rec_len<float>(M), x, mom, t_dev,
+                                                   dt_dev, cs, lam0sq, four_nu, (float*)rec);
+  } else {
+    prep_kernel<double><<<blocks, threads, 0, st>>>(n, M, K, rec_len<double>(M), x, mom, t_dev,
+                                                    dt_dev, cs, lam0sq, four_nu, (double*)rec);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const FinishArgs& A, cudaStream_t st) {
+  const int TB = A.targets_per_block;
+  const size_t smem = sizeof(double) * ((size_t)TB * (A.NB + A.K + 3) + 2 * A.M + 3);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(finish_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int blocks = (A.n + TB - 1) / TB;
+  finish_kernel<<<blocks, 128, smem, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_time(double* t_dev, const double* dt_dev, cudaStream_t st) {
+  advance_time_kernel<<<1, 32, 0, st>>>(t_dev, dt_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(int n, int K, const double* x, const double* mom, int* flags,
+                        cudaStream_t st) {
+  scan_state_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, K, x, mom, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace mmvm

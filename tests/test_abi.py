@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every symbol include/mmvm.h declares.
+
+No compute calls (this runs without a GPU).  The header is parsed for its
+function declarations so a new entry point cannot be forgotten in the binding.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mmvm.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mmvm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1010_2475_gb300 as mm
+    from paper_1010_2475_gb300 import build
+
+    build.build(verbose=False)
+    return mm.load_library()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "mmvm_create" in names and "mmvm_step" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    import paper_1010_2475_gb300 as mm
+
+    assert sorted(mm.EXPORTS) == names
+
+
+def test_exports_have_c_linkage(lib):
+    import paper_1010_2475_gb300 as mm
+
+    out = subprocess.run(["nm", "-D", "--defined-only", mm.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    syms = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    for name in _declared():
+        assert name in syms, f"{name} not exported unmangled"
+
+
+def test_pure_host_entry_points(lib):
+    import paper_1010_2475_gb300 as mm
+
+    assert lib.mmvm_num_moments(6) == 28
+    assert lib.mmvm_num_moments(60) == 1891
+    assert lib.mmvm_num_particles(None) == 0
+    # an invalid config is rejected before any device call
+    cfg = mm.mmvm_config(-1, 0, 1.0, 0.0, 0, 0)
+    h = ctypes.c_void_p()
+    assert lib.mmvm_create(ctypes.byref(cfg), ctypes.byref(h)) == mm.MMVM_E_INVALID_ARG
+    assert b"order" in lib.mmvm_last_error()
+    cfg = mm.mmvm_config(2, 7, 1.0, 0.0, 0, 0)
+    assert lib.mmvm_create(ctypes.byref(cfg), ctypes.byref(h)) == mm.MMVM_E_INVALID_ARG
+    cfg = mm.mmvm_config(99, 0, 1.0, 0.0, 0, 0)
+    assert lib.mmvm_create(ctypes.byref(cfg), ctypes.byref(h)) == mm.MMVM_E_UNSUPPORTED
+    cfg = mm.mmvm_config(2, 0, -1.0, 0.0, 0, 0)
+    assert lib.mmvm_create(ctypes.byref(cfg), ctypes.byref(h)) == mm.MMVM_E_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    import paper_1010_2475_gb300 as mm
+
+    with pytest.raises(RuntimeError, match="missing"):
+        old = mm._lib_handle
+        mm._lib_handle = None
+        try:
+            mm.load_library(str(tmp_path / "libmmvm.so"))
+        finally:
+            mm._lib_handle = old

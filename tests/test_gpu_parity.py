@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (stated in the design notes):
+* FP64 mode: 1e-12 relative (weighted moment norm / velocity max norm) for a
+  single right-hand side, and after RK4 steps.
+* Mixed FP32 mode: 2e-6 relative for a single right-hand side (the FP32 jet
+  is exact to a few hundred FP32 ulps of the largest entry of each order);
+  1e-5 relative on moments after 100 RK4 steps.
+Sizes span several CTA tiles of targets and sources and end in ragged tails;
+at the full benchmark sizes a sample of target rows is checked against the
+oracle's sum over every source.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mmvm_inputs
+from oracle.rhs import lam_at, rhs_literal, rhs_regrouped, rk4
+from tests.parity_util import rhs_error, state_error, vel_error
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_RHS_TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def mm():
+    import paper_1010_2475_gb300 as mm
+
+    mm.load_library()
+    return mm
+
+
+def _gpu_rhs(mm, wl, t, prec):
+    with mm.Context(wl.order, wl.lam0, wl.nu, prec) as ctx:
+        ctx.set_state(wl.x, wl.moments, t)
+        return ctx.rhs()
+
+
+@pytest.mark.parametrize("order", [0, 2, 4, 6, 10])
+def test_single_particle_rhs_fp64(mm, order):
+    wl = mmvm_inputs.single_quadrupole(order=order, eps=0.1, sigma0=1.0)
+    rng = np.random.default_rng(order)
+    wl.moments[0, 3:] += rng.normal(size=wl.K - 3) * 0.02 if wl.K > 3 else 0.0
+    ox, oM = rhs_regrouped(wl.x, wl.moments, 1.5, order, wl.lam0, wl.nu)
+    gx, gM = _gpu_rhs(mm, wl, 1.5, mm.MMVM_FP64)
+    assert np.all(gx == 0.0)
+    lam = lam_at(1.5, wl.lam0, wl.nu)
+    if order >= 2:
+        assert rhs_error(gM, oM, order, lam) <= FP64_TOL
+
+
+@pytest.mark.parametrize("order,n", [(0, 2), (1, 5), (2, 37), (3, 70), (4, 131), (6, 97), (8, 40)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_multi_particle_rhs(mm, order, n, prec):
+    wl = mmvm_inputs.random_disk(n=n, order=order, radius=2.0 + 0.15 * n ** 0.5, sigma=0.45,
+                                 amp=0.03, seed=100 + order)
+    t = 0.7
+    ox, oM = rhs_regrouped(wl.x, wl.moments, t, order, wl.lam0, wl.nu)
+    p = mm.MMVM_FP64 if prec == "fp64" else mm.MMVM_MIXED_FP32
+    gx, gM = _gpu_rhs(mm, wl, t, p)
+    tol = FP64_TOL if prec == "fp64" else MIXED_RHS_TOL
+    lam = lam_at(t, wl.lam0, wl.nu)
+    assert vel_error(gx, ox) <= tol
+    if order >= 2:
+        assert rhs_error(gM, oM, order, lam) <= tol
+
+
+def test_literal_form_small(mm):
+    """Tiny case against the literal Gamma-tensor form (no regrouping)."""
+    wl = mmvm_inputs.random_disk(n=4, order=3, radius=1.5, sigma=0.6, amp=0.05, seed=5)
+    ox, oM = rhs_literal(wl.x, wl.moments, 0.0, 3, wl.lam0, wl.nu)
+    gx, gM = _gpu_rhs(mm, wl, 0.0, mm.MMVM_FP64)
+    assert vel_error(gx, ox) <= FP64_TOL
+    assert rhs_error(gM, oM, 3, wl.lam0) <= FP64_TOL
+
+
+def test_near_coincident_and_far_pairs(mm):
+    """Separations from 1e-7 core sizes to 1e4 core sizes (both jet paths)."""
+    order = 4
+    x = np.array([[0.0, 0.0], [1e-7, 2e-7], [0.3, -0.1], [2.0, 1.0], [40.0, -30.0],
+                  [900.0, 1200.0]])
+    rng = np.random.default_rng(9)
+    K = (order + 1) * (order + 2) // 2
+    mom = rng.normal(size=(6, K)) * 0.05
+    mom[:, 0] = [1.0, -0.7, 0.4, 0.9, -1.1, 0.5]
+    mom[:, 1:3] = 0.0
+    lam0, nu, t = 0.2, 1e-3, 0.0
+    ox, oM = rhs_regrouped(x, mom, t, order, lam0, nu)
+    with mm.Context(order, lam0, nu, mm.MMVM_FP64) as ctx:
+        ctx.set_state(x, mom, t)
+        gx, gM = ctx.rhs()
+    assert vel_error(gx, ox) <= FP64_TOL
+    assert rhs_error(gM, oM, order, lam0) <= FP64_TOL
+
+
+def test_rk4_fp64_matches_oracle(mm):
+    wl = mmvm_inputs.random_disk(n=24, order=3, radius=2.0, sigma=0.5, amp=0.03, seed=3)
+    dt, nsteps = 0.02, 5
+    ox, oM, ot = rk4(wl.x, wl.moments, 0.0, dt, nsteps, 3, wl.lam0, wl.nu)
+    with mm.Context(3, wl.lam0, wl.nu, mm.MMVM_FP64) as ctx:
+        ctx.set_state(wl.x, wl.moments, 0.0)
+        ctx.step(dt, nsteps)
+        gx, gM, gt = ctx.get_state()
+    assert gt == pytest.approx(ot, rel=1e-15)
+    lam = lam_at(ot, wl.lam0, wl.nu)
+    assert np.abs(gx - ox).max() / lam <= FP64_TOL
+    assert state_error(gM, oM, 3, lam) <= FP64_TOL
+
+
+def test_rk4_mixed_100_steps(mm):
+    """Mixed precision: <= 1e-5 relative on moments after 100 RK4 steps.
+
+    Two co-rotating patches of 24 particles (higher moments start at 0 and
+    grow to ~2.5% of the circulation over the run)."""
+    wl = mmvm_inputs.two_patches(n=48, order=4, sigma=0.35, seed=11)
+    dt, nsteps = 0.05, 100
+    ox, oM, ot = rk4(wl.x, wl.moments, 0.0, dt, nsteps, 4, wl.lam0, wl.nu)
+    with mm.Context(4, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32) as ctx:
+        ctx.set_state(wl.x, wl.moments, 0.0)
+        ctx.step(dt, nsteps)
+        gx, gM, gt = ctx.get_state()
+    lam = lam_at(ot, wl.lam0, wl.nu)
+    assert state_error(gM, oM, 4, lam) <= 1e-5
+    assert np.abs(gx - ox).max() / lam <= 1e-5
+
+
+def test_single_particle_config_steps(mm):
+    """Single particle, order 10 (the M=10 quadrupole case), 50 FP64 steps."""
+    wl = mmvm_inputs.single_quadrupole(order=10, eps=0.1, sigma0=1.0, Re=1000.0)
+    ox, oM, ot = rk4(wl.x, wl.moments, 0.0, 0.01, 50, 10, wl.lam0, wl.nu)
+    with mm.Context(10, wl.lam0, wl.nu, mm.MMVM_FP64) as ctx:
+        ctx.set_state(wl.x, wl.moments, 0.0)
+        ctx.step(0.01, 50)
+        gx, gM, gt = ctx.get_state()
+    assert state_error(gM, oM, 10, lam_at(ot, wl.lam0, wl.nu)) <= FP64_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_random_disk_full_size_sampled_rows(mm, prec):
+    """N = 4096, M = 4 random disk: sampled target rows against all sources."""
+    wl = mmvm_inputs.random_disk()
+    p = mm.MMVM_FP64 if prec == "fp64" else mm.MMVM_MIXED_FP32
+    gx, gM = _gpu_rhs(mm, wl, 0.0, p)
+    rows = np.random.default_rng(1).choice(wl.n, 12, replace=False)
+    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=rows)
+    tol = FP64_TOL if prec == "fp64" else MIXED_RHS_TOL
+    assert vel_error(gx[rows], ox) <= tol
+    assert rhs_error(gM[rows], oM, wl.order, wl.lam0) <= tol
+
+
+def test_two_patches_full_size_sampled_rows(mm):
+    """N = 65536, M = 6 two patches (mixed precision): sampled rows vs oracle."""
+    wl = mmvm_inputs.two_patches()
+    gx, gM = _gpu_rhs(mm, wl, 0.0, mm.MMVM_MIXED_FP32)
+    assert np.all(np.isfinite(gM)) and np.all(np.isfinite(gx))
+    rows = np.random.default_rng(2).choice(wl.n, 4, replace=False)
+    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=rows)
+    assert vel_error(gx[rows], ox) <= MIXED_RHS_TOL
+    # total impulse sum_j M00 xdot^j vanishes (pair antisymmetry) at any size
+    imp = (wl.moments[:, :1] * gx).sum(0)
+    assert np.abs(imp).max() <= 1e-6 * np.abs(wl.moments[:, :1] * gx).sum()
+
+
+def test_error_codes(mm):
+    wl = mmvm_inputs.random_disk(n=8, order=2, seed=1)
+    with mm.Context(2, wl.lam0, wl.nu, mm.MMVM_FP64) as ctx:
+        bad = wl.moments.copy()
+        bad[3, 0] = 0.0
+        with pytest.raises(mm.MMVMError) as ei:
+            ctx.set_state(wl.x, bad, 0.0)
+        assert ei.value.code == mm.MMVM_E_ZERO_CIRCULATION
+        bad = wl.moments.copy()
+        bad[2, 4] = np.nan
+        with pytest.raises(mm.MMVMError) as ei:
+            ctx.set_state(wl.x, bad, 0.0)
+        assert ei.value.code == mm.MMVM_E_NUMERIC
+    with mm.Context(10, 1.0, 0.0, mm.MMVM_FP64) as ctx:
+        K = 66
+        with pytest.raises(mm.MMVMError) as ei:
+            ctx.set_state(np.zeros((2, 2)), np.ones((2, K)), 0.0)
+        assert ei.value.code == mm.MMVM_E_UNSUPPORTED

@@ -101,3 +101,20 @@ def test_tensor_parity_and_homogeneity(order):
     direct = gamma_tensor(order, lam, J1, J2)
     scaled = self_tensor(order, lam)
     assert np.abs(direct - scaled).max() <= 1e-13 * np.abs(direct).max()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_finish_term_scaling(order):
+    """The regrouped form's term list at lambda equals a direct build at lambda."""
+    from oracle.coefficients import c_k, gamma_I_terms, gamma_II_terms
+    from oracle.rhs import _finish_terms
+
+    lam = 0.77
+    ks, ls, cs, comps, offs = _finish_terms(order, lam)
+    direct = []
+    for ki, (k1, k2) in enumerate(multi_indices(order)):
+        for li, (l1, l2) in enumerate(multi_indices(order)):
+            for terms in (gamma_I_terms(k1, k2, l1, l2, lam), gamma_II_terms(k1, k2, l1, l2, lam)):
+                for coef, _ in terms:
+                    direct.append(c_k(k1, k2, lam) * coef)
+    np.testing.assert_allclose(cs, np.array(direct), rtol=1e-14, atol=0)
