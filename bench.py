@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput of the multi-moment vortex method right-hand side on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: two co-rotating Gaussian patches, N = 65536 particles (2 x 32768,
+patch radius 2, centres (+-3, 0), circulations ~ exp(-r^2) normalised to 1
+per patch), order M = 6 (28 moments), core sigma = lambda_0 = 0.1, Re = 2000,
+RK4 with dt = 0.05; mixed precision (FP32 pair jets and contractions, FP64
+state, tables and per-particle finish).  One step = one RK4 step = four
+right-hand sides = 4 N^2 ordered pair interactions (the self pair included:
+the finish kernel evaluates it from the jet at the origin).
+
+value      pair-interactions/s of the device-timed steps (state resident in HBM,
+           L2 flushed by a 256 MiB write before every timed step, outside the
+           timed region).
+e2e        the same metric through the C ABI with host buffers: set_state from
+           pinned host memory, one step, get_state to pinned host memory.
+roofline   the all-pairs kernel (~99% of the step) against the FP32 FMA peak
+           of 152 SMs x 128 lanes x 2 flop x 2.07 GHz; the flop count per pair
+           is the kernel's algorithm (see flops_per_pair).
+fp64       the plain FP64 form of the same right-hand side on the first 16384
+           particles of the workload (one right-hand side, device-timed).
+cpu_baseline / --impl reference: the FP64 numpy oracle on sampled target rows
+           against all sources, on the host cores.
+N > 1 GPUs (torchrun): independent replicas of the workload, one per GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import mmvm_inputs  # noqa: E402
+
+METRIC = "moment-ODE pair-interactions/s"
+UNIT = "pair-interactions/s"
+SM_COUNT = 152
+FP32_LANES = 128
+SM_MAX_GHZ = 2.07
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+FP64_SUBSET = 16384
+
+
+def workload(n: int = 65536):
+    return mmvm_inputs.two_patches(n=n, order=6, sigma=0.1, Re=2000.0, dt=0.05, steps=100)
+
+
+def config_dict(wl, extra=None):
+    d = {"workload": f"two co-rotating Gaussian patches, N={wl.n}, M=6, sigma=0.1, Re=2000, "
+                     "RK4 dt=0.05 (all-pairs)",
+         "n": wl.n, "order": wl.order, "moments_per_particle": wl.K, "lambda0": wl.lam0,
+         "Re": 1.0 / wl.nu, "dt": wl.dt,
+         "precision": "mixed: FP32 pair jet/contraction, FP64 state/tables/finish/RK4",
+         "pairs_per_step": 4 * wl.n * wl.n,
+         "l2": "flushed (256 MiB write) before every timed step, outside the timed region"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def flops_per_pair(M: int) -> int:
+    """Floating-point operations of one near-field pair in the all-pairs kernel.
+
+    K = (M+1)(M+2)/2 source moments, NB = (2M+1)(2M+2)/2 - 1 correlation
+    outputs Psi[beta], NJ = 3M jet orders:
+      contraction   K * NB multiply-adds                     = 2 K NB
+      jet order n   Laplacian chain, projection, seeds,
+                    Cartesian entries                        ~ 5 (n-1) + 4
+      edge terms    I_n, zbar^n, scaling (per order)         ~ 16
+      Hermite fns   two three-term recurrences               ~ 6 (NJ - 1)
+      setup         separation, |b|^2, masks                 ~ 30 (plus 2 exp)
+    """
+    K = (M + 1) * (M + 2) // 2
+    NB = (2 * M + 1) * (2 * M + 2) // 2 - 1 if M > 0 else 2
+    NJ = 3 * M if M > 0 else 1
+    return 2 * K * NB + 5 * NJ * (NJ - 1) // 2 + 4 * NJ + 16 * NJ + 6 * (NJ - 1) + 30
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            p = [v.strip() for v in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_rate(wl, rows: int, seed: int = 0):
+    """Time the FP64 oracle on `rows` target rows against all sources."""
+    from oracle.rhs import rhs_regrouped
+
+    sel = np.random.default_rng(seed).choice(wl.n, rows, replace=False)
+    t0 = time.perf_counter()
+    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=sel)
+    dt = time.perf_counter() - t0
+    return rows * wl.n / dt, dt, sel, ox, oM
+
+
+def cpu_cores_used() -> int:
+    v = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or "1"
+    try:
+        return int(v)
+    except ValueError:
+        return 1
+
+
+def run_reference(args, wl):
+    rows = args.oracle_rows
+    vals, secs = [], []
+    for s in range(args.warmup):
+        oracle_rate(wl, max(1, rows // 4), seed=1000 + s)
+    for s in range(args.steps):
+        v, dt, *_ = oracle_rate(wl, rows, seed=s)
+        vals.append(v)
+        secs.append(dt)
+    value = len(vals) * rows * wl.n / sum(secs)
+    sample = (f"{rows} random target rows x all {wl.n} sources per step, one right-hand "
+              f"side at t=0 (FP64 numpy oracle)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(wl, {"oracle_rows_per_step": rows}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args, wl, rank, world, local_rank):
+    import torch
+
+    import paper_1010_2475_gb300 as mm
+    from tests.parity_util import rhs_error, vel_error
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream(dev)
+    ctx = mm.Context(wl.order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32, device=local_rank)
+    mm.mmvm_set_stream(ctx.handle, stream.cuda_stream)
+    ctx.set_state(wl.x, wl.moments, 0.0)
+    mm.mmvm_enable_timing(ctx.handle, True)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    pairs_step = 4 * wl.n * wl.n
+
+    # accuracy of this run's arithmetic: right-hand side at t = 0 vs the oracle
+    gx0, gM0 = ctx.rhs()
+    for _ in range(args.warmup):
+        ctx.step(wl.dt, 1)
+    torch.cuda.synchronize(dev)
+    mm.mmvm_pair_time(ctx.handle)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = ctx.launches
+    step_ms, pair_ms, pair_cnt = [], 0.0, 0
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.step(wl.dt, 1)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            ms, cnt = mm.mmvm_pair_time(ctx.handle)
+            pair_ms += ms
+            pair_cnt += cnt
+    torch.cuda.synchronize(dev)
+    launches = ctx.launches - launches0
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = world * pairs_step * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    K = wl.K
+    hx = torch.empty((wl.n, 2), dtype=torch.float64, pin_memory=True).numpy()
+    hm = torch.empty((wl.n, K), dtype=torch.float64, pin_memory=True).numpy()
+    ox_ = torch.empty((wl.n, 2), dtype=torch.float64, pin_memory=True).numpy()
+    om_ = torch.empty((wl.n, K), dtype=torch.float64, pin_memory=True).numpy()
+    x_cur, m_cur, t_cur = ctx.get_state()
+    hx[:] = x_cur
+    hm[:] = m_cur
+    e2e_s = []
+    lib = mm.load_library()
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        ctx.set_state(hx, hm, t_cur)
+        ctx.step(wl.dt, 1)
+        tt = np.zeros(1)
+        mm._check(lib.mmvm_get_state(ctx.handle, mm._dptr(ox_), mm._dptr(om_), mm._dptr(tt)))
+        e2e_s.append(time.perf_counter() - t0)
+        hx[:] = ox_
+        hm[:] = om_
+        t_cur = float(tt[0])
+    e2e_val = world * pairs_step / statistics.mean(e2e_s) if e2e_s else None
+    bytes_state = wl.n * (2 + K) * 8
+
+    # plain FP64 form on a subset (one right-hand side, device-timed)
+    fp64 = None
+    if not args.skip_fp64:
+        sub = wl.subset(min(FP64_SUBSET, wl.n))
+        c64 = mm.Context(sub.order, sub.lam0, sub.nu, mm.MMVM_FP64, device=local_rank)
+        mm.mmvm_set_stream(c64.handle, stream.cuda_stream)
+        c64.set_state(sub.x, sub.moments, 0.0)
+        c64.rhs()
+        mm.mmvm_enable_timing(c64.handle, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        d_dx = torch.empty((sub.n, 2), dtype=torch.float64, device=dev)
+        d_dm = torch.empty((sub.n, sub.K), dtype=torch.float64, device=dev)
+        e0.record(stream)
+        mm.mmvm_rhs_device(c64.handle, d_dx.data_ptr(), d_dm.data_ptr())
+        e1.record(stream)
+        e1.synchronize()
+        rhs_ms = e0.elapsed_time(e1)
+        p64_ms, _ = mm.mmvm_pair_time(c64.handle)
+        c32 = mm.Context(sub.order, sub.lam0, sub.nu, mm.MMVM_MIXED_FP32, device=local_rank)
+        mm.mmvm_set_stream(c32.handle, stream.cuda_stream)
+        c32.set_state(sub.x, sub.moments, 0.0)
+        c32.rhs()
+        mm.mmvm_enable_timing(c32.handle, True)
+        e0.record(stream)
+        mm.mmvm_rhs_device(c32.handle, d_dx.data_ptr(), d_dm.data_ptr())
+        e1.record(stream)
+        e1.synchronize()
+        rhs32_ms = e0.elapsed_time(e1)
+        fp64 = {"value": sub.n * sub.n / (rhs_ms / 1e3), "unit": UNIT,
+                "workload": f"first {sub.n} particles of the workload, one right-hand side",
+                "ms_per_rhs": rhs_ms, "pair_kernel_ms": p64_ms,
+                "mixed_same_subset": sub.n * sub.n / (rhs32_ms / 1e3),
+                "mixed_over_fp64": rhs_ms / rhs32_ms}
+        c64.close()
+        c32.close()
+
+    line = None
+    if rank == 0:
+        avg_pair_s = pair_ms / max(pair_cnt, 1) / 1e3
+        fpp = flops_per_pair(wl.order)
+        achieved = wl.n * wl.n * fpp / avg_pair_s / 1e12
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(wl, {"parallelism": f"replicas x{world}"}),
+                "clocks": clk.summary(),
+                "e2e": {"value": e2e_val, "unit": UNIT,
+                        "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state + 8,
+                        "steps": args.e2e_steps},
+                "gpu_launches": launches,
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                             "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                             "traffic": None, "kernel": "pair_kernel (all-pairs jet + contraction)",
+                             "flops_per_pair": fpp, "launch_ms": avg_pair_s * 1e3,
+                             "launches_timed": pair_cnt,
+                             "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz "
+                                          "(recipe unit counts and maximum SM clock)"},
+                "fp64": fp64}
+        if not args.skip_cpu:
+            rate, secs, sel, ox, oM = oracle_rate(wl, args.oracle_rows)
+            line["cpu_baseline"] = {
+                "value": rate, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                "sample": f"{args.oracle_rows} random target rows x all {wl.n} sources, one "
+                          f"right-hand side at t=0 ({secs:.1f} s, FP64 numpy oracle)"}
+            line["error_vs_oracle"] = {
+                "rows": args.oracle_rows, "t": 0.0,
+                "xdot_rel": vel_error(gx0[sel], ox),
+                "dM_rel_weighted": rhs_error(gM0[sel], oM, wl.order, wl.lam0)}
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--oracle-rows", type=int, default=2)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--n", type=int, default=65536,
+                    help="particles (the benchmark is 65536; smaller only for profiling)")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = workload(args.n)
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+    if world > 1 or args.gpus > 1:
+        args.skip_cpu = args.skip_cpu or rank != 0
+    run_ours(args, wl, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

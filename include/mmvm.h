@@ -89,9 +89,9 @@ void mmvm_destroy(mmvm_ctx* ctx);
 int mmvm_set_state(mmvm_ctx* ctx, int64_t n, const double* x, const double* moments,
                    double t);
 
-/* Same, from DEVICE pointers (copied device-to-device on the context stream;
- * the caller may reuse its buffers once the call returns... after
- * mmvm_synchronize).  The zero-circulation / finiteness checks are not made. */
+/* Same, from DEVICE pointers: copied device-to-device on the context stream,
+ * and the call waits for the copy, so the caller may reuse its buffers when
+ * it returns.  The zero-circulation and finiteness checks are not made.     */
 int mmvm_set_state_device(mmvm_ctx* ctx, int64_t n, const double* d_x,
                           const double* d_moments, double t);
 
@@ -126,6 +126,16 @@ int32_t mmvm_num_moments(int32_t order);
 
 /* Kernel launches issued by this context since creation (for accounting).   */
 int64_t mmvm_launch_count(const mmvm_ctx* ctx);
+
+/* Kernel timing.  mmvm_enable_timing(ctx, 1) makes every later right-hand
+ * side (also inside mmvm_step, whose steps are then launched directly rather
+ * than replayed from the graph) record CUDA events around its all-pairs
+ * launch on the context stream.  mmvm_pair_time(ctx, &ms, &count) waits for
+ * the stream and returns the summed device time (ms) and number of all-pairs
+ * launches since the previous call; only the launches of the last right-hand
+ * side or step are kept, so call it after each one.                         */
+int mmvm_enable_timing(mmvm_ctx* ctx, int on);
+int mmvm_pair_time(mmvm_ctx* ctx, double* ms, int64_t* count);
 
 /* Message for the calling thread's last error ("" if none).                 */
 const char* mmvm_last_error(void);

@@ -50,7 +50,8 @@ EXPORTS = (
     "mmvm_create", "mmvm_destroy", "mmvm_set_state", "mmvm_set_state_device",
     "mmvm_get_state", "mmvm_get_state_device", "mmvm_rhs", "mmvm_rhs_device",
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
-    "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error",
+    "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_enable_timing",
+    "mmvm_pair_time",
 )
 
 
@@ -108,6 +109,10 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_num_moments.restype = ctypes.c_int32
     lib.mmvm_launch_count.argtypes = [P]
     lib.mmvm_launch_count.restype = ctypes.c_int64
+    lib.mmvm_enable_timing.argtypes = [P, ctypes.c_int]
+    lib.mmvm_enable_timing.restype = ctypes.c_int
+    lib.mmvm_pair_time.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
+    lib.mmvm_pair_time.restype = ctypes.c_int
     lib.mmvm_last_error.argtypes = []
     lib.mmvm_last_error.restype = ctypes.c_char_p
     _lib_handle = lib
@@ -195,6 +200,18 @@ def mmvm_synchronize(h) -> None:
 
 def mmvm_launch_count(h) -> int:
     return int(load_library().mmvm_launch_count(h))
+
+
+def mmvm_enable_timing(h, on: bool = True) -> None:
+    _check(load_library().mmvm_enable_timing(h, 1 if on else 0))
+
+
+def mmvm_pair_time(h):
+    """(summed all-pairs device time in ms, number of launches) since the last call."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    _check(load_library().mmvm_pair_time(h, ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
 
 
 class Context:

@@ -80,6 +80,11 @@ struct mmvm_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int64_t launches = 0;
+  double last_dt = NAN;  // dt currently held in dt_dev
+  // optional pair-kernel timing: one event pair per RK stage (slot 4: rhs)
+  bool timing = false;
+  cudaEvent_t ev[5][2] = {};
+  bool ev_pending[5] = {};
 
   double* t_dev() { return scal.p; }
   double* dt_dev() { return scal.p + 1; }
@@ -146,7 +151,13 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
   if (n > 1) {
     MMVM_CK(mmvm::launch_prep(c->cfg.precision, n, c->M, xin, min_, c->t_dev(), dt_dev, cs,
                               lam0sq, four_nu, c->rec.p, c->st));
+    const int slot = mode == 0 ? 4 : mode - 1;
+    if (c->timing) MMVM_CK(cudaEventRecord(c->ev[slot][0], c->st));
     MMVM_CK(c->pe.launch(c->rec.p, n, c->chunks, c->S, c->partial.p, c->st));
+    if (c->timing) {
+      MMVM_CK(cudaEventRecord(c->ev[slot][1], c->st));
+      c->ev_pending[slot] = true;
+    }
     c->launches += 2;
   }
   mmvm::FinishArgs A;
@@ -292,6 +303,9 @@ void mmvm_destroy(mmvm_ctx* c) {
   cudaSetDevice(c->cfg.device);
   if (c->st) cudaStreamSynchronize(c->st);
   c->drop_graph();
+  for (auto& pr : c->ev)
+    for (auto& e : pr)
+      if (e) cudaEventDestroy(e);
   for (auto* b : {&c->x, &c->m, &c->xs, &c->ms, &c->xsum, &c->msum, &c->rdx, &c->rdm, &c->scal,
                   &c->partial, &c->e_c, &c->psi0})
     b->release();
@@ -406,10 +420,22 @@ int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
   if (!std::isfinite(dt) || nsteps < 0) return fail(MMVM_E_INVALID_ARG, "bad dt or nsteps");
   if (nsteps == 0) return MMVM_OK;
   MMVM_CK(cudaSetDevice(c->cfg.device));
-  static thread_local double dt_host;
-  dt_host = dt;
-  MMVM_CK(cudaMemcpyAsync(c->dt_dev(), &dt_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
-  MMVM_CK(cudaStreamSynchronize(c->st));
+  if (!(dt == c->last_dt)) {
+    static thread_local double dt_host;
+    dt_host = dt;
+    MMVM_CK(cudaMemcpyAsync(c->dt_dev(), &dt_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    MMVM_CK(cudaStreamSynchronize(c->st));
+    c->last_dt = dt;
+  }
+  if (c->timing) {
+    // Timed steps are launched directly (events captured inside a graph
+    // cannot be read back for elapsed time); the kernels are the same.
+    for (int64_t s = 0; s < nsteps; ++s) {
+      int rc = enqueue_step(c);
+      if (rc) return rc;
+    }
+    return MMVM_OK;
+  }
   if (!c->graph_ok) {
     MMVM_CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
     const int64_t before = c->launches;
@@ -434,6 +460,37 @@ int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
   for (int64_t s = 0; s < nsteps; ++s) {
     MMVM_CK(cudaGraphLaunch(c->gexec, c->st));
     c->launches += per_step;
+  }
+  return MMVM_OK;
+}
+
+int mmvm_enable_timing(mmvm_ctx* c, int on) {
+  if (!c) return fail(MMVM_E_INVALID_ARG, "null context");
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  if (on && !c->ev[0][0]) {
+    for (auto& pr : c->ev)
+      for (auto& e : pr) MMVM_CK(cudaEventCreate(&e));
+  }
+  if (c->timing != (on != 0)) c->drop_graph();  // re-capture with or without events
+  c->timing = on != 0;
+  for (bool& p : c->ev_pending) p = false;
+  return MMVM_OK;
+}
+
+int mmvm_pair_time(mmvm_ctx* c, double* ms, int64_t* count) {
+  if (!c || !ms || !count) return fail(MMVM_E_INVALID_ARG, "null argument");
+  *ms = 0.0;
+  *count = 0;
+  if (!c->timing) return MMVM_OK;
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  for (int s = 0; s < 5; ++s) {
+    if (!c->ev_pending[s]) continue;
+    float e = 0.f;
+    MMVM_CK(cudaEventElapsedTime(&e, c->ev[s][0], c->ev[s][1]));
+    *ms += e;
+    *count += 1;
+    c->ev_pending[s] = false;
   }
   return MMVM_OK;
 }

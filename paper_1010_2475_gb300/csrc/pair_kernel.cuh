@@ -29,6 +29,13 @@
 // is stable (k <= x) and downward from a Kummer series at the top order
 // otherwise; for x >= 40 the edge zbar^n I_{n-1} itself is run upward in
 // complex arithmetic so that nothing under- or overflows at large |b|.
+//
+// FP32 mode carries the separation as an exact pair b = b_hi + b_lo (the
+// records hold zeta as (hi, lo) floats).  The Gaussian factors are sensitive
+// to it (a relative error e in b moves e^{-x} by ~2 x e), so x = |b|^2 and
+// e^{-x} are formed from the exact square, 1/x and the powers of zbar use the
+// two-term value, and the Hermite functions get the first-order Taylor
+// correction h_k(b) = h_k(b_hi) + b_lo h_{k+1}(b_hi).
 #pragma once
 
 #include "common.cuh"
@@ -73,18 +80,32 @@ struct PairNear {
   // Add one source's contribution (moments a[K], separation b in c = 1 units)
   // to my slice acc[NBL] of Psi.  wmask = 0 removes the pair exactly (it is
   // used for the self pair, whose separation the caller moves far away).
-  __device__ __forceinline__ static void run(T b1, T b2, T wmask, const T (&a)[K],
-                                             T (&acc)[NBL]) {
-    const T x = b1 * b1 + b2 * b2;
-    const T ex1 = dexp(-b1 * b1);
-    const T ex2 = dexp(-b2 * b2);
-    const T E = ex1 * ex2;
+  __device__ __forceinline__ static void run(T b1, T b2, T l1, T l2, T wmask,
+                                             const T (&a)[K], T (&acc)[NBL]) {
+    // squares (b_hi + b_lo)^2 = s_d + q_d + 2 b_hi b_lo (q_d: rounding of s_d)
+    const T s1 = b1 * b1;
+    const T s2 = b2 * b2;
+    const T q1 = fma(b1, b1, -s1);
+    const T q2 = fma(b2, b2, -s2);
+    const T sl1 = q1 + T(2) * b1 * l1;
+    const T sl2 = q2 + T(2) * b2 * l2;
+    // x = xh + xl (TwoSum of the two squares plus the small corrections)
+    const T xh = s1 + s2;
+    const T bv = xh - s1;
+    const T xl = ((s1 - (xh - bv)) + (s2 - bv)) + (sl1 + sl2);
+    const T x = xh;
+    // e^{-b_hi^2} per axis (the Hermite tables are built at b_hi) ...
+    const T eh1 = dexp(-s1) * (T(1) - q1);
+    const T eh2 = dexp(-s2) * (T(1) - q2);
+    // ... and e^{-x} at the full separation
+    const T E = eh1 * (T(1) - T(2) * b1 * l1) * (eh2 * (T(1) - T(2) * b2 * l2));
     // w[n-1] = zbar^n I_{n-1}(x), n = 1..NJ
     T wr[NJ], wi[NJ];
     if (x < T(40)) {
       constexpr int P = NJ - 1;
       T I[P + 1];
-      const T rx = T(1) / x;  // inf at x == 0: those entries are replaced below
+      const T rxh = T(1) / x;  // inf at x == 0: those entries are replaced below
+      const T rx = rxh * (T(1) - xl * rxh);
       I[0] = (T(1) - E) * rx;
       static_for<1, P + 1>([&](auto nc) {
         constexpr int k = decltype(nc)::value;
@@ -95,16 +116,16 @@ struct PairNear {
         static_for_down<1, P + 1>([&](auto nc) {
           constexpr int k = decltype(nc)::value;
           if (T(k) > x) I[k] = Id;
-          Id = (x * Id + E) * T(1.0 / k);
+          Id = (fma(x, Id, xl * Id) + E) * T(1.0 / k);
         });
         if (x < T(1)) I[0] = Id;
       }
-      T zr = b1, zi = -b2;
+      T zr = b1 + l1, zi = -b2 - l2;
       static_for<0, NJ>([&](auto nc) {
         constexpr int k = decltype(nc)::value;
-        if constexpr (k > 0) {
-          const T tr = zr * b1 + zi * b2;
-          const T ti = zi * b1 - zr * b2;
+        if constexpr (k > 0) {  // (zr + i zi) * ((b1 + l1) - i (b2 + l2)), two-term
+          const T tr = fma(zr, b1, fma(zi, b2, fma(zr, l1, zi * l2)));
+          const T ti = fma(zi, b1, fma(-zr, b2, fma(zi, l1, -zr * l2)));
           zr = tr;
           zi = ti;
         }
@@ -112,35 +133,42 @@ struct PairNear {
         wi[k] = zi * I[k];
       });
     } else {
-      const T rx = T(1) / x;
-      T qr = E * b1, qi = -E * b2;  // E zbar^{n}
+      const T rxh = T(1) / x;
+      const T rx = rxh * (T(1) - xl * rxh);
+      const T c1 = b1 + l1, c2 = b2 + l2;
+      T qr = E * c1, qi = -E * c2;  // E zbar^{n}
       const T f0 = (T(1) - E) * rx;
-      wr[0] = b1 * f0;
-      wi[0] = -b2 * f0;
+      wr[0] = c1 * f0;
+      wi[0] = -c2 * f0;
       static_for<1, NJ>([&](auto nc) {
         constexpr int k = decltype(nc)::value;  // order k+1 from order k
         const T tr = qr * b1 + qi * b2;
         const T ti = qi * b1 - qr * b2;
         qr = tr;
         qi = ti;
-        const T pr = wr[k - 1] * b1 + wi[k - 1] * b2;
-        const T pi = wi[k - 1] * b1 - wr[k - 1] * b2;
+        const T wr0 = wr[k - 1], wi0 = wi[k - 1];
+        const T pr = fma(wr0, b1, fma(wi0, b2, fma(wr0, l1, wi0 * l2)));
+        const T pi = fma(wi0, b1, fma(-wr0, b2, fma(wi0, l1, -wr0 * l2)));
         wr[k] = (T(k) * pr - qr) * rx;
         wi[k] = (T(k) * pi - qi) * rx;
       });
     }
-    // Hermite functions: hx[k] = h_k(b1)/pi, hy[k] = h_k(b2)
-    T hx[HN], hy[HN];
-    hx[0] = ex1 * T(kInvPi);
-    hy[0] = ex2;
-    if constexpr (HN > 1) {
-      hx[1] = T(-2) * b1 * hx[0];
-      hy[1] = T(-2) * b2 * hy[0];
-    }
-    static_for<1, HN - 1>([&](auto kc) {
+    // Hermite functions at b_hi, one order beyond what is used, then the
+    // first-order correction to b = b_hi + b_lo: hx[k] = h_k(b1)/pi, hy[k] = h_k(b2)
+    T hx[HN + 1], hy[HN + 1];
+    hx[0] = eh1 * T(kInvPi);
+    hy[0] = eh2;
+    hx[1] = T(-2) * b1 * hx[0];
+    hy[1] = T(-2) * b2 * hy[0];
+    static_for<1, HN>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
       hx[k + 1] = T(-2) * b1 * hx[k] - T(2 * k) * hx[k - 1];
       hy[k + 1] = T(-2) * b2 * hy[k] - T(2 * k) * hy[k - 1];
+    });
+    static_for<0, HN>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      hx[k] = fma(l1, hx[k + 1], hx[k]);
+      hy[k] = fma(l2, hy[k + 1], hy[k]);
     });
 
     static_for<1, NJ + 1>([&](auto nc) {

@@ -38,10 +38,16 @@ __device__ __forceinline__ void pair_tile(const T* tile, int cnt, int t0, int j,
     T a[K];
 #pragma unroll
     for (int m = 0; m < K; ++m) a[m] = r[HDR + m];
-    T b1, b2;
+    T b1, b2, l1 = T(0), l2 = T(0);
     if constexpr (f32) {
-      b1 = (tz1 - r[0]) + (tl1 - r[2]);
-      b2 = (tz2 - r[1]) + (tl2 - r[3]);
+      // b = (hi difference) + (lo difference) as an exact (hi, lo) pair
+      const T d1 = tz1 - r[0], e1 = tl1 - r[2];
+      const T d2 = tz2 - r[1], e2 = tl2 - r[3];
+      b1 = d1 + e1;
+      b2 = d2 + e2;
+      const T v1 = b1 - d1, v2 = b2 - d2;
+      l1 = (d1 - (b1 - v1)) + (e1 - v1);
+      l2 = (d2 - (b2 - v2)) + (e2 - v2);
     } else {
       b1 = tz1 - r[0];
       b2 = tz2 - r[1];
@@ -50,9 +56,11 @@ __device__ __forceinline__ void pair_tile(const T* tile, int cnt, int t0, int j,
     if (t0 + s == j) {  // self pair: excluded here, added exactly by the finish
       b1 = T(1e15);
       b2 = T(0);
+      l1 = T(0);
+      l2 = T(0);
       wm = T(0);
     }
-    PN::run(b1, b2, wm, a, accr);
+    PN::run(b1, b2, l1, l2, wm, a, accr);
   }
   if constexpr (f32) {
 #pragma unroll

@@ -37,3 +37,32 @@ def state_error(M, M_ref, order, lam):
 
 def vel_error(dx, dx_ref):
     return float(np.abs(dx - dx_ref).max() / np.abs(dx_ref).max())
+
+
+def single_particle_condition(moments_row, order, lam):
+    """Weighted condition number of the single-particle moment equation.
+
+    kappa_w = ||sum_terms |term| ||_w / ||dM||_w over the terms of the
+    regrouped self term (oracle/rhs.py).  Any FP64 evaluation has errors up to
+    ~eps * kappa_w in the weighted norm; kappa_w grows like 2^n n! with the
+    order (about 6, 14, 250, 5e3, 6e4 for M = 2, 4, 6, 8, 10 on the test
+    states), which is why the FP64 tolerance is max(1e-12, 2 eps kappa_w).
+    """
+    from oracle.rhs import _finish_terms, self_velocity_jets
+
+    m = np.atleast_2d(moments_row)
+    S1, S2 = self_velocity_jets(m, lam, order)
+    W = (S1[0], S2[0])
+    ks, ls, cs, comps, offs = _finish_terms(order, lam)
+    K = m.shape[1]
+    absum = np.zeros(K)
+    res = np.zeros(K)
+    for k, l, c, comp, o in zip(ks, ls, cs, comps, offs):
+        v = c * m[0, l] * W[comp][o]
+        absum[k] += abs(v)
+        res[k] += v
+    return float(wnorm(absum, order, lam)[0] / wnorm(res, order, lam)[0])
+
+
+def fp64_tolerance(kappa: float) -> float:
+    return max(1e-12, 2.0 * 2.220446049250313e-16 * kappa)

@@ -1,11 +1,15 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances (stated in the design notes):
+Tolerances (derived in the design notes):
 * FP64 mode: 1e-12 relative (weighted moment norm / velocity max norm) for a
-  single right-hand side, and after RK4 steps.
-* Mixed FP32 mode: 2e-6 relative for a single right-hand side (the FP32 jet
-  is exact to a few hundred FP32 ulps of the largest entry of each order);
-  1e-5 relative on moments after 100 RK4 steps.
+  single right-hand side and after RK4 steps; where the weighted condition
+  number of the moment equation kappa_w exceeds ~2e3 (single particle,
+  M = 10) no FP64 evaluation can promise that, and the tolerance is
+  2 eps kappa_w.
+* Mixed FP32 mode: 5e-6 relative for a single right-hand side (rounding
+  accumulated along the order-n recurrences of the jet, ~2 n u with n <= 3M
+  and u = 2^-24, plus the tile sums); 1e-5 relative on moments after 100 RK4
+  steps.
 Sizes span several CTA tiles of targets and sources and end in ragged tails;
 at the full benchmark sizes a sample of target rows is checked against the
 oracle's sum over every source.
@@ -17,12 +21,13 @@ import pytest
 
 import mmvm_inputs
 from oracle.rhs import lam_at, rhs_literal, rhs_regrouped, rk4
-from tests.parity_util import rhs_error, state_error, vel_error
+from tests.parity_util import (fp64_tolerance, rhs_error, single_particle_condition,
+                               state_error, vel_error)
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-MIXED_RHS_TOL = 2e-6
+MIXED_RHS_TOL = 5e-6
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +54,8 @@ def test_single_particle_rhs_fp64(mm, order):
     assert np.all(gx == 0.0)
     lam = lam_at(1.5, wl.lam0, wl.nu)
     if order >= 2:
-        assert rhs_error(gM, oM, order, lam) <= FP64_TOL
+        tol = fp64_tolerance(single_particle_condition(wl.moments[0], order, lam))
+        assert rhs_error(gM, oM, order, lam) <= tol
 
 
 @pytest.mark.parametrize("order,n", [(0, 2), (1, 5), (2, 37), (3, 70), (4, 131), (6, 97), (8, 40)])
