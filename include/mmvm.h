@@ -63,13 +63,20 @@ extern "C" {
 #define MMVM_MAX_ORDER_PAIRS 8
 #define MMVM_MAX_ORDER_SINGLE 16
 
+/* mmvm_config.flags bits.  In MMVM_MIXED_FP32 mode the particles are put in
+ * spatial (Morton) order every step and tile pairs whose bounding boxes are
+ * far enough apart that the Gaussian part of the pair jet is below FP32
+ * rounding take the point-vortex jet (far field); this flag turns that off
+ * (every pair takes the full jet).  MMVM_FP64 never uses the far field.     */
+#define MMVM_FLAG_NO_FAR_FIELD 1u
+
 typedef struct mmvm_config {
   int32_t order;        /* truncation order M >= 0                            */
   int32_t precision;    /* MMVM_FP64 or MMVM_MIXED_FP32                       */
   double lambda0;       /* core size lambda_0 > 0 at t = 0 (eq:phi00)        */
   double nu;            /* kinematic viscosity >= 0 (Re = Gamma_ref / nu)     */
   int32_t device;       /* CUDA device ordinal                                */
-  uint32_t flags;       /* reserved, must be 0                                */
+  uint32_t flags;       /* MMVM_FLAG_* bits, other bits must be 0             */
 } mmvm_config;
 
 typedef struct mmvm_ctx mmvm_ctx;
@@ -136,6 +143,28 @@ int64_t mmvm_launch_count(const mmvm_ctx* ctx);
  * side or step are kept, so call it after each one.                         */
 int mmvm_enable_timing(mmvm_ctx* ctx, int on);
 int mmvm_pair_time(mmvm_ctx* ctx, double* ms, int64_t* count);
+
+/* All-pairs kernel configuration in use for the loaded state: out[0..5] =
+ * variant index, order slices (kernels per evaluation), targets per CTA,
+ * CTAs per SM of the register budget, per-source barrier (0/1), source
+ * chunks.  The variant is
+ * chosen by timing every compiled variant on the first state of each size
+ * class (environment: MMVM_PAIR_VARIANT=<v> forces one, MMVM_AUTOTUNE=0
+ * keeps variant 0).                                                         */
+int mmvm_pair_config(const mmvm_ctx* ctx, int32_t* out);
+
+/* Cumulative counts of ordered pairs the all-pairs kernel evaluated since the
+ * context was created, by path: full jet (near) and point-vortex multipoles
+ * (far, MMVM_MIXED_FP32 only).  The self pair and the tuning launches are not
+ * counted.  Waits for the context stream.                                   */
+int mmvm_pair_counts(mmvm_ctx* ctx, int64_t* near_pairs, int64_t* far_pairs);
+
+/* Measured fused-multiply-add peak of a device, in flop/s (2 flops per FMA):
+ * a full-occupancy grid of independent FMA chains, about 50 ms, timed with
+ * CUDA events on a stream of its own.  precision selects the FP64 or the
+ * FP32 pipe.  A calibration of the hardware for roofline fractions, not part
+ * of the method.  Returns MMVM_E_DEVICE on a CUDA error.                     */
+int mmvm_alu_peak(int32_t device, int32_t precision, double* flops_per_s);
 
 /* Message for the calling thread's last error ("" if none).                 */
 const char* mmvm_last_error(void);

@@ -32,6 +32,7 @@ MMVM_E_TIMEOUT = -6
 MMVM_E_DEVICE = -7
 MMVM_FP64 = 0
 MMVM_MIXED_FP32 = 1
+MMVM_FLAG_NO_FAR_FIELD = 1
 MMVM_MAX_ORDER_PAIRS = 8
 MMVM_MAX_ORDER_SINGLE = 16
 
@@ -51,7 +52,7 @@ EXPORTS = (
     "mmvm_get_state", "mmvm_get_state_device", "mmvm_rhs", "mmvm_rhs_device",
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
     "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_enable_timing",
-    "mmvm_pair_time",
+    "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_counts", "mmvm_alu_peak",
 )
 
 
@@ -113,6 +114,14 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_enable_timing.restype = ctypes.c_int
     lib.mmvm_pair_time.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
     lib.mmvm_pair_time.restype = ctypes.c_int
+    lib.mmvm_alu_peak.argtypes = [ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.POINTER(ctypes.c_double)]
+    lib.mmvm_alu_peak.restype = ctypes.c_int
+    lib.mmvm_pair_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int64)]
+    lib.mmvm_pair_counts.restype = ctypes.c_int
+    lib.mmvm_pair_config.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.mmvm_pair_config.restype = ctypes.c_int
     lib.mmvm_last_error.argtypes = []
     lib.mmvm_last_error.restype = ctypes.c_char_p
     _lib_handle = lib
@@ -135,8 +144,8 @@ def n_moments(order: int) -> int:
 
 
 def mmvm_create(order: int, lambda0: float, nu: float, precision: int = MMVM_FP64,
-                device: int = 0) -> ctypes.c_void_p:
-    cfg = mmvm_config(order, precision, lambda0, nu, device, 0)
+                device: int = 0, flags: int = 0) -> ctypes.c_void_p:
+    cfg = mmvm_config(order, precision, lambda0, nu, device, flags)
     h = ctypes.c_void_p()
     _check(load_library().mmvm_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h
@@ -214,13 +223,36 @@ def mmvm_pair_time(h):
     return ms.value, cnt.value
 
 
+def mmvm_alu_peak(device: int = 0, precision: int = MMVM_MIXED_FP32) -> float:
+    """Measured FMA peak of the device in flop/s (FP32 or FP64 pipe)."""
+    v = ctypes.c_double()
+    _check(load_library().mmvm_alu_peak(device, precision, ctypes.byref(v)))
+    return v.value
+
+
+def mmvm_pair_counts(h):
+    """(near pairs, far pairs) evaluated by the all-pairs kernel so far."""
+    a = ctypes.c_int64()
+    b = ctypes.c_int64()
+    _check(load_library().mmvm_pair_counts(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def mmvm_pair_config(h) -> dict:
+    """Variant of the all-pairs kernel in use (see include/mmvm.h)."""
+    out = (ctypes.c_int32 * 6)()
+    _check(load_library().mmvm_pair_config(h, out))
+    return dict(zip(("variant", "order_slices", "targets_per_cta", "ctas_per_sm",
+                     "sync", "chunks"), list(out)))
+
+
 class Context:
     """Owning wrapper of an mmvm_ctx handle."""
 
     def __init__(self, order: int, lambda0: float, nu: float, precision: int = MMVM_FP64,
-                 device: int = 0):
+                 device: int = 0, flags: int = 0):
         self.order = order
-        self.handle = mmvm_create(order, lambda0, nu, precision, device)
+        self.handle = mmvm_create(order, lambda0, nu, precision, device, flags)
 
     def set_state(self, x, moments, t=0.0):
         mmvm_set_state(self.handle, x, moments, t)

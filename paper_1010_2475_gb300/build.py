@@ -37,14 +37,34 @@ def _headers():
     return hs
 
 
+def _n_variants(m: int, p: int) -> int:
+    """Mirror of n_variants() in csrc/pair_variants.h."""
+    if p == 0:
+        return 1
+    return 1 if m <= 3 else (2 if m == 7 else (4 if m == 6 else 3))
+
+
+def _n_slices(m: int, p: int, v: int) -> int:
+    """Mirror of variant_spec(m, p, v).nslices in csrc/pair_variants.h."""
+    if p == 0:
+        return {0: 1, 1: 1, 2: 1, 3: 1, 4: 2, 5: 2, 6: 3, 7: 4, 8: 4}[m]
+    if m <= 3:
+        return 1
+    return {4: [1, 1, 2], 5: [1, 2, 2], 6: [1, 2, 3, 2], 7: [2, 3], 8: [3, 4, 4]}[m][v]
+
+
 def _units():
     """(source, object, extra flags) for every translation unit."""
     units = []
     for m in range(MAX_ORDER_PAIRS + 1):
         for p in (0, 1):
-            units.append(("pair_inst.cu", f"pair_m{m}_p{p}.o",
-                          [f"-DMMVM_INST_M={m}", f"-DMMVM_INST_PREC={p}"]))
-    for src in ("pair_registry.cu", "particle_kernels.cu", "api.cu", "tables.cpp"):
+            for v in range(_n_variants(m, p)):
+                for sl in range(_n_slices(m, p, v)):
+                    units.append(("pair_inst.cu", f"pair_m{m}_p{p}_v{v}_s{sl}.o",
+                                  [f"-DMMVM_INST_M={m}", f"-DMMVM_INST_PREC={p}",
+                                   f"-DMMVM_INST_V={v}", f"-DMMVM_INST_S={sl}"]))
+    for src in ("pair_registry.cu", "particle_kernels.cu", "order.cu", "api.cu", "calibrate.cu",
+                "tables.cpp"):
         units.append((src, os.path.splitext(src)[0] + ".o", []))
     return units
 
@@ -72,6 +92,9 @@ def build(jobs: int | None = None, force: bool = False, verbose: bool = True) ->
     units = _units()
     # heaviest variants first so the pool stays busy
     units.sort(key=lambda u: -int(u[1].split("_m")[1].split("_")[0]) if u[1].startswith("pair_m") else 0)
+    stale = [f for f in os.listdir(BUILD) if f.endswith(".o") and f not in {u[1] for u in units}]
+    for f in stale:  # objects of variants that no longer exist
+        os.remove(os.path.join(BUILD, f))
     objs = []
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         futs = [ex.submit(_compile, nvcc, s, o, e, force) for s, o, e in units]

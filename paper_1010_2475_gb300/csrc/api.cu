@@ -11,8 +11,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/mmvm.h"
@@ -63,14 +67,23 @@ struct DevBuf {
 
 }  // namespace
 
+namespace mmvm {
+// Record the calling thread's last error message (for other files of the library).
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace mmvm
+
 struct mmvm_ctx {
   mmvm_config cfg{};
   int M = 0, K = 0, NB = 0;
   int64_t n = 0;
   cudaStream_t own = nullptr, st = nullptr;
   DevBuf<double> x, m, xs, ms, xsum, msum, rdx, rdm, scal, partial;
-  DevBuf<unsigned char> rec;
-  DevBuf<int> flags, k_off, e_l, e_b;
+  DevBuf<unsigned char> rec, order_tmp;
+  DevBuf<int> flags, k_off, e_l, e_b, perm;
+  DevBuf<float> gbox;  // float4 per group of kGroup sorted positions
+  DevBuf<unsigned long long> counts;  // cumulative (near, far) pairs of the all-pairs kernel
+  bool far = false;    // FP32 and not MMVM_FLAG_NO_FAR_FIELD: sort + far-field tiles
+  int order_launches = 0;  // kernels launched by one spatial ordering
   DevBuf<double> e_c, psi0;
   mmvm::PairEntry pe;
   int S = 32;            // sources per shared-memory tile
@@ -104,8 +117,7 @@ int choose_chunks(const mmvm_ctx* c, int64_t n) {
   if (n <= 1) return 0;
   int dev_sms = 0;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
-  int per_sm = 1;
-  if (c->pe.occupancy) c->pe.occupancy(c->S, &per_sm);
+  int per_sm = c->pe.nslices ? mmvm::pair_occupancy(c->pe, c->S) : 1;
   per_sm = std::max(per_sm, 1);
   const int64_t tiles = (n + c->pe.tpc - 1) / c->pe.tpc;
   const int64_t slots = (int64_t)std::max(dev_sms, 1) * per_sm;
@@ -114,6 +126,19 @@ int choose_chunks(const mmvm_ctx* c, int64_t n) {
   const int64_t max_ch = std::max<int64_t>(1, n / (4 * c->S));
   ch = std::min(std::max<int64_t>(ch, 1), max_ch);
   return (int)ch;
+}
+
+// Process-wide autotuning results: (device, M, precision, far, log2 n) -> variant.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
+
+int ilog2(int64_t v) {
+  int r = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++r;
+  }
+  return r;
 }
 
 int ensure_buffers(mmvm_ctx* c, int64_t n) {
@@ -134,7 +159,34 @@ int ensure_buffers(mmvm_ctx* c, int64_t n) {
   if (n > 1) {
     c->chunks = choose_chunks(c, n);
     MMVM_CK(grow(c->rec, (size_t)n * c->pe.rec_len * c->pe.elem_bytes));
-    MMVM_CK(grow(c->partial, (size_t)c->chunks * c->NB * n));
+    MMVM_CK(grow(c->partial, (size_t)std::max(c->chunks, 4) * c->NB * n));
+    if (c->far) {
+      MMVM_CK(grow(c->perm, (size_t)n));
+      MMVM_CK(grow(c->gbox, (size_t)4 * ((n + mmvm::kGroup - 1) / mmvm::kGroup)));
+      MMVM_CK(grow(c->order_tmp, mmvm::spatial_order_temp_bytes((int)n)));
+      if (realloc) {
+        // count the kernels one ordering launches (the sort's are the library's)
+        cudaGraph_t g = nullptr;
+        MMVM_CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = mmvm::launch_spatial_order((int)n, c->x.p, c->order_tmp.p,
+                                                    c->order_tmp.cap, c->perm.p, c->st);
+        cudaError_t e2 = cudaStreamEndCapture(c->st, &g);
+        if (e1 != cudaSuccess) return cuda_fail(e1, "spatial order");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture(order)");
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        int kn = 0;
+        for (auto nd : nodes) {
+          cudaGraphNodeType ty;
+          cudaGraphNodeGetType(nd, &ty);
+          if (ty == cudaGraphNodeTypeKernel) ++kn;
+        }
+        c->order_launches = kn;
+        cudaGraphDestroy(g);
+      }
+    }
   } else {
     c->chunks = 0;
   }
@@ -148,12 +200,21 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
   const int n = (int)c->n;
   const double lam0sq = c->cfg.lambda0 * c->cfg.lambda0;
   const double four_nu = 4.0 * c->cfg.nu;
+  const int* perm = (n > 1 && c->far) ? c->perm.p : nullptr;
   if (n > 1) {
-    MMVM_CK(mmvm::launch_prep(c->cfg.precision, n, c->M, xin, min_, c->t_dev(), dt_dev, cs,
-                              lam0sq, four_nu, c->rec.p, c->st));
+    if (c->far && (mode == 0 || mode == 1)) {  // order from the step-start centres
+      MMVM_CK(mmvm::launch_spatial_order(n, xin, c->order_tmp.p, c->order_tmp.cap, c->perm.p,
+                                         c->st));
+      c->launches += c->order_launches;
+    }
+    MMVM_CK(mmvm::launch_prep(c->cfg.precision, n, c->M, perm, xin, min_, c->t_dev(), dt_dev,
+                              cs, lam0sq, four_nu, c->rec.p, c->far ? c->gbox.p : nullptr,
+                              c->st));
     const int slot = mode == 0 ? 4 : mode - 1;
     if (c->timing) MMVM_CK(cudaEventRecord(c->ev[slot][0], c->st));
-    MMVM_CK(c->pe.launch(c->rec.p, n, c->chunks, c->S, c->partial.p, c->st));
+    MMVM_CK(mmvm::pair_launch(c->pe, c->rec.p, n, c->chunks, c->S,
+                              c->far ? c->gbox.p : nullptr, c->partial.p, 0, c->st,
+                              c->counts.p));
     if (c->timing) {
       MMVM_CK(cudaEventRecord(c->ev[slot][1], c->st));
       c->ev_pending[slot] = true;
@@ -168,6 +229,7 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
   A.nchunks = n > 1 ? c->chunks : 0;
   A.targets_per_block = c->finish_tb;
   A.partial = n > 1 ? c->partial.p : nullptr;
+  A.perm = perm;
   A.Min = min_;
   A.k_off = c->k_off.p;
   A.e_l = c->e_l.p;
@@ -202,6 +264,101 @@ int enqueue_step(mmvm_ctx* c) {
   if ((rc = enqueue_rhs(c, 4, c->xs.p, c->ms.p, 1.0, dt))) return rc;
   MMVM_CK(mmvm::launch_advance_time(c->t_dev(), dt, c->st));
   c->launches += 1;
+  return MMVM_OK;
+}
+
+// Pick the all-pairs variant for this (order, precision, size class): time
+// each compiled variant on the current records (every target tile against the
+// first few 1024-source chunks, at least two waves of CTAs) and keep the
+// fastest per pair.  MMVM_PAIR_VARIANT=<v> forces a variant, MMVM_AUTOTUNE=0
+// keeps variant 0.  Runs outside any stream capture (from set_state).
+int tune_pair(mmvm_ctx* c) {
+  const int n = (int)c->n;
+  const int nv = mmvm::pair_variant_count(c->M, c->cfg.precision);
+  if (n <= 1 || nv <= 1) return MMVM_OK;
+  const auto key = std::make_tuple(c->cfg.device, c->M, c->cfg.precision, c->far ? 1 : 0,
+                                   ilog2(n));
+  int choice = -1;
+  if (const char* f = std::getenv("MMVM_PAIR_VARIANT")) choice = std::atoi(f);
+  if (choice < 0) {
+    if (const char* a = std::getenv("MMVM_AUTOTUNE"))
+      if (std::atoi(a) == 0) choice = 0;
+  }
+  if (choice < 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) choice = it->second;
+  }
+  if (choice < 0) {
+    // records of the current state
+    const double lam0sq = c->cfg.lambda0 * c->cfg.lambda0, four_nu = 4.0 * c->cfg.nu;
+    const int* perm = c->far ? c->perm.p : nullptr;
+    if (c->far)
+      MMVM_CK(mmvm::launch_spatial_order(n, c->x.p, c->order_tmp.p, c->order_tmp.cap, c->perm.p,
+                                         c->st));
+    MMVM_CK(mmvm::launch_prep(c->cfg.precision, n, c->M, perm, c->x.p, c->m.p, c->t_dev(),
+                              nullptr, 0.0, lam0sq, four_nu, c->rec.p,
+                              c->far ? c->gbox.p : nullptr, c->st));
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
+    cudaEvent_t e0, e1;
+    MMVM_CK(cudaEventCreate(&e0));
+    MMVM_CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    choice = 0;
+    for (int v = 0; v < nv; ++v) {
+      mmvm::PairEntry e = mmvm::pair_entry(c->M, c->cfg.precision, v);
+      if (e.M != c->M) continue;
+      if (mmvm::pair_prepare(e, c->S) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      const int per_sm = mmvm::pair_occupancy(e, c->S);
+      if (per_sm < 1) continue;
+      const int tiles = (n + e.tpc - 1) / e.tpc;
+      const int chunks = std::max(1, n / 1024);
+      const int chunk_len = mmvm::round_up((n + chunks - 1) / chunks, c->S);
+      const int gy = std::min({chunks, 4, std::max(1, (2 * dev_sms * per_sm + tiles - 1) / tiles)});
+      const void* gb = c->far ? c->gbox.p : nullptr;
+      MMVM_CK(mmvm::pair_launch(e, c->rec.p, n, chunks, c->S, gb, c->partial.p, gy, c->st));
+      MMVM_CK(cudaEventRecord(e0, c->st));
+      MMVM_CK(mmvm::pair_launch(e, c->rec.p, n, chunks, c->S, gb, c->partial.p, gy, c->st));
+      MMVM_CK(cudaEventRecord(e1, c->st));
+      MMVM_CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      MMVM_CK(cudaEventElapsedTime(&ms, e0, e1));
+      const double pairs = (double)n * std::min((double)gy * chunk_len, (double)n);
+      const double per_pair = ms / pairs;
+      if (const char* vb = std::getenv("MMVM_TUNE_VERBOSE"))
+        if (std::atoi(vb))
+          std::fprintf(stderr, "[mmvm tune] M=%d prec=%d n=%d variant %d (slices=%d TPC=%d "
+                       "MINB=%d SYNC=%d, %d CTAs/SM): %.3f ms, %.3e pairs/s\n", c->M,
+                       c->cfg.precision, n, v, e.nslices, e.tpc, e.minb, e.sync, per_sm, ms,
+                       pairs / (ms * 1e-3));
+      if (per_pair < best) {
+        best = per_pair;
+        choice = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = choice;
+  }
+  mmvm::PairEntry e = mmvm::pair_entry(c->M, c->cfg.precision, choice);
+  if (e.M != c->M) return fail(MMVM_E_INVALID_ARG, "MMVM_PAIR_VARIANT out of range");
+  if (e.variant != c->pe.variant || !c->pe.nslices) {
+    MMVM_CK(mmvm::pair_prepare(e, c->S));
+    c->pe = e;
+    c->drop_graph();
+  }
+  const int ch = choose_chunks(c, n);
+  if ((size_t)ch * c->NB * n > c->partial.cap) {
+    MMVM_CK(c->partial.ensure((size_t)ch * c->NB * n));
+    c->drop_graph();
+  }
+  if (ch != c->chunks) c->drop_graph();
+  c->chunks = ch;
   return MMVM_OK;
 }
 
@@ -244,7 +401,7 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
     return fail(MMVM_E_INVALID_ARG, "lambda0 must be positive and finite");
   if (!(cfg->nu >= 0.0) || !std::isfinite(cfg->nu))
     return fail(MMVM_E_INVALID_ARG, "nu must be >= 0 and finite");
-  if (cfg->flags != 0) return fail(MMVM_E_INVALID_ARG, "flags must be 0");
+  if (cfg->flags & ~MMVM_FLAG_NO_FAR_FIELD) return fail(MMVM_E_INVALID_ARG, "unknown flag bits");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -255,11 +412,12 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
 
   mmvm_ctx* c = new mmvm_ctx();
   c->cfg = *cfg;
+  c->far = cfg->precision == MMVM_MIXED_FP32 && !(cfg->flags & MMVM_FLAG_NO_FAR_FIELD);
   c->M = cfg->order;
   c->K = mmvm::n_moments(c->M);
   c->NB = mmvm::n_beta(c->M);
   if (c->M <= MMVM_MAX_ORDER_PAIRS) {
-    c->pe = mmvm::pair_entry(c->M, cfg->precision);
+    c->pe = mmvm::pair_entry(c->M, cfg->precision, 0);
     if (c->pe.M != c->M) {
       delete c;
       return fail(MMVM_E_UNSUPPORTED, "pair kernel variant not compiled");
@@ -267,6 +425,7 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
   }
   const int K = c->K;
   c->finish_tb = std::max(1, 128 / (((K + 31) / 32) * 32));
+  c->S = mmvm::kGroup;
   auto bail = [&](int rc) {
     mmvm_destroy(c);
     return rc;
@@ -280,7 +439,8 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
       (e = c->e_b.ensure(T.e_b.size())) != cudaSuccess ||
       (e = c->e_c.ensure(T.e_c.size())) != cudaSuccess ||
       (e = c->psi0.ensure(T.psi0.size())) != cudaSuccess ||
-      (e = c->scal.ensure(2)) != cudaSuccess || (e = c->flags.ensure(2)) != cudaSuccess)
+      (e = c->scal.ensure(2)) != cudaSuccess || (e = c->flags.ensure(2)) != cudaSuccess ||
+      (e = c->counts.ensure(2)) != cudaSuccess)
     return bail(cuda_fail(e, "cudaMalloc(tables)"));
   auto up = [&](void* d, const void* h, size_t bytes) {
     return bytes ? cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
@@ -290,9 +450,10 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
       (e = up(c->e_b.p, T.e_b.data(), T.e_b.size() * sizeof(int))) != cudaSuccess ||
       (e = up(c->e_c.p, T.e_c.data(), T.e_c.size() * sizeof(double))) != cudaSuccess ||
       (e = up(c->psi0.p, T.psi0.data(), T.psi0.size() * sizeof(double))) != cudaSuccess ||
-      (e = cudaMemset(c->scal.p, 0, 2 * sizeof(double))) != cudaSuccess)
+      (e = cudaMemset(c->scal.p, 0, 2 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMemset(c->counts.p, 0, 2 * sizeof(unsigned long long))) != cudaSuccess)
     return bail(cuda_fail(e, "cudaMemcpy(tables)"));
-  if (c->pe.prepare && (e = c->pe.prepare(c->S)) != cudaSuccess)
+  if (c->pe.nslices && (e = mmvm::pair_prepare(c->pe, c->S)) != cudaSuccess)
     return bail(cuda_fail(e, "pair kernel shared-memory limit"));
   *out = c;
   return MMVM_OK;
@@ -310,6 +471,10 @@ void mmvm_destroy(mmvm_ctx* c) {
                   &c->partial, &c->e_c, &c->psi0})
     b->release();
   c->rec.release();
+  c->counts.release();
+  c->order_tmp.release();
+  c->perm.release();
+  c->gbox.release();
   c->flags.release();
   c->k_off.release();
   c->e_l.release();
@@ -355,6 +520,8 @@ static int set_state_common(mmvm_ctx* c, int64_t n, const double* x, const doubl
   static thread_local double t_host;
   t_host = t;
   MMVM_CK(cudaMemcpyAsync(c->t_dev(), &t_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  rc = tune_pair(c);
+  if (rc) return rc;
   MMVM_CK(cudaStreamSynchronize(c->st));
   return MMVM_OK;
 }
@@ -456,11 +623,33 @@ int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
     }
     c->graph_ok = true;
   }
-  const int per_step = (c->n > 1 ? 12 : 4) + 1;
+  const int per_step = (c->n > 1 ? 12 + (c->far ? c->order_launches : 0) : 4) + 1;
   for (int64_t s = 0; s < nsteps; ++s) {
     MMVM_CK(cudaGraphLaunch(c->gexec, c->st));
     c->launches += per_step;
   }
+  return MMVM_OK;
+}
+
+int mmvm_pair_counts(mmvm_ctx* c, int64_t* near_pairs, int64_t* far_pairs) {
+  if (!c || !near_pairs || !far_pairs) return fail(MMVM_E_INVALID_ARG, "null argument");
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  unsigned long long h[2] = {0, 0};
+  MMVM_CK(cudaMemcpyAsync(h, c->counts.p, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  *near_pairs = (int64_t)h[0];
+  *far_pairs = (int64_t)h[1];
+  return MMVM_OK;
+}
+
+int mmvm_pair_config(const mmvm_ctx* c, int32_t* out) {
+  if (!c || !out) return fail(MMVM_E_INVALID_ARG, "null argument");
+  out[0] = c->pe.variant;
+  out[1] = c->pe.nslices;
+  out[2] = c->pe.tpc;
+  out[3] = c->pe.minb;
+  out[4] = c->pe.sync;
+  out[5] = c->chunks;
   return MMVM_OK;
 }
 

@@ -46,10 +46,29 @@ template <> struct Rec<double> {
   static constexpr int HDR = 2;  // z1, z2
 };
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+// FP32 records also carry the far-field moments A'_n (n = 0..M, complex).
+template <typename T>
+__host__ __device__ constexpr int rec_far(int M) {
+  return sizeof(T) == 4 ? 2 * (M + 1) : 0;
+}
 template <typename T>
 __host__ __device__ constexpr int rec_len(int M) {
   // pad to 16 bytes so a record (and a tile of records) can be bulk-copied
-  return round_up(Rec<T>::HDR + n_moments(M), 16 / (int)sizeof(T));
+  return round_up(Rec<T>::HDR + n_moments(M) + rec_far<T>(M), 16 / (int)sizeof(T));
+}
+
+// Particles per spatial group: the source tile of the pair kernel and the
+// unit of the bounding boxes used for the far-field test.
+constexpr int kGroup = 32;
+
+// Far-field threshold on x = |b|^2 (c = 1 units) per order M: beyond it the
+// Gaussian part of every jet entry of order <= 3M is below 2^-25 of the
+// largest entry of that order (measured against the FP64 oracle's jet over
+// all directions; 6 units of margin added), so a tile pair whose bounding
+// boxes are this far apart uses the point-vortex jet.
+__host__ __device__ constexpr float x_far(int M) {
+  return M <= 0 ? 20.f : M == 1 ? 32.f : M == 2 ? 40.f : M == 3 ? 50.f : M == 4 ? 58.f
+       : M == 5 ? 66.f : M == 6 ? 74.f : M == 7 ? 80.f : 88.f;
 }
 
 // Compile-time loop: f(std::integral_constant<int, i>) for i in [B, E).

@@ -1,14 +1,13 @@
-// One compiled variant of the all-pairs kernel.  Built once per (order,
-// precision) with -DMMVM_INST_M=<order> -DMMVM_INST_PREC=<0|1> so the
-// variants compile in parallel.
+// One order slice of one variant of the all-pairs kernel.  Built once per
+// (order, precision, variant, slice) with -DMMVM_INST_M, -DMMVM_INST_PREC,
+// -DMMVM_INST_V and -DMMVM_INST_S so the kernels compile in parallel.
 #include "pair_launch.cuh"
 #include "pair_registry.h"
+#include "pair_variants.h"
 
-#ifndef MMVM_INST_M
-#error "MMVM_INST_M must be defined"
-#endif
-#ifndef MMVM_INST_PREC
-#error "MMVM_INST_PREC must be defined"
+#if !defined(MMVM_INST_M) || !defined(MMVM_INST_PREC) || !defined(MMVM_INST_V) || \
+    !defined(MMVM_INST_S)
+#error "MMVM_INST_M, MMVM_INST_PREC, MMVM_INST_V and MMVM_INST_S must be defined"
 #endif
 
 namespace mmvm {
@@ -16,43 +15,41 @@ namespace mmvm {
 namespace {
 constexpr int kM = MMVM_INST_M;
 using T = std::conditional_t<MMVM_INST_PREC == 1, float, double>;
-// Output slices per target (G) and targets per CTA: chosen so the per-thread
-// accumulators and one jet order fit in registers without spilling.
-constexpr int kG = (MMVM_INST_PREC == 1) ? (kM <= 6 ? 1 : 2)
-                                         : (kM <= 3 ? 1 : (kM <= 6 ? 2 : 4));
-constexpr int kTPC = (MMVM_INST_PREC == 1) ? (kG == 1 ? 128 : 64) : 32;
+constexpr VariantSpec kSpec = variant_spec(kM, MMVM_INST_PREC, MMVM_INST_V);
+static_assert(MMVM_INST_S < kSpec.nslices, "slice index out of range");
+constexpr int kLO = kSpec.s[MMVM_INST_S].lo;
+constexpr int kHI = kSpec.s[MMVM_INST_S].hi;
+constexpr int kTPC = kSpec.TPC;
+constexpr int kMINB = kSpec.MINB;
+constexpr bool kSYNC = kSpec.SYNC != 0;
+static_assert(kTPC % 32 == 0, "targets per CTA must be whole warps");
+#define MMVM_KERNEL pair_kernel<kM, T, kLO, kHI, kTPC, kMINB, kSYNC>
 
-size_t smem_fn(int S) { return pair_smem_bytes<kM, T, kG, kTPC>(S); }
+size_t smem_fn(int S) { return pair_smem_bytes<kM, T, kLO, kHI, kTPC>(S); }
 cudaError_t prepare_fn(int S) {
-  return cudaFuncSetAttribute(pair_kernel<kM, T, kG, kTPC>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fn(S));
+  return cudaFuncSetAttribute(MMVM_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_fn(S));
 }
-cudaError_t launch_fn(const void* rec, int n, int chunks, int S, double* partial,
-                      cudaStream_t st) {
-  const int chunk_len = (n + chunks - 1) / chunks;
-  dim3 grid((n + kTPC - 1) / kTPC, chunks);
-  pair_kernel<kM, T, kG, kTPC><<<grid, kTPC * kG, smem_fn(S), st>>>(
-      static_cast<const T*>(rec), n, chunk_len, S, partial);
+cudaError_t launch_fn(const void* rec, int n, int chunk_len, int gy, int S, const void* gbox,
+                      double* partial, unsigned long long* counts, cudaStream_t st) {
+  dim3 grid((n + kTPC - 1) / kTPC, gy);
+  MMVM_KERNEL<<<grid, kTPC, smem_fn(S), st>>>(static_cast<const T*>(rec), n, chunk_len, S,
+                                              static_cast<const float4*>(gbox), partial, counts);
   return cudaGetLastError();
 }
 cudaError_t occ_fn(int S, int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, pair_kernel<kM, T, kG, kTPC>,
-                                                       kTPC * kG, smem_fn(S));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, MMVM_KERNEL, kTPC, smem_fn(S));
 }
 }  // namespace
 
-#define MMVM_CAT3(a, b, c) a##b##c
-#define MMVM_ENTRY_NAME(m, p) MMVM_CAT3(pair_entry_m, m, _p##p)
-#define MMVM_ENTRY(m, p) MMVM_ENTRY_NAME(m, p)
+#define MMVM_CAT5(a, b, c, d, e) a##b##c##d##e
+#define MMVM_SLICE_NAME(m, p, v, s) MMVM_CAT5(pair_slice_m, m, _p##p, _v##v, _s##s)
+#define MMVM_SLICE(m, p, v, s) MMVM_SLICE_NAME(m, p, v, s)
 
-PairEntry MMVM_ENTRY(MMVM_INST_M, MMVM_INST_PREC)() {
-  PairEntry e;
-  e.M = kM;
-  e.precision = MMVM_INST_PREC;
-  e.tpc = kTPC;
-  e.g = kG;
-  e.rec_len = rec_len<T>(kM);
-  e.elem_bytes = (int)sizeof(T);
+SliceEntry MMVM_SLICE(MMVM_INST_M, MMVM_INST_PREC, MMVM_INST_V, MMVM_INST_S)() {
+  SliceEntry e;
+  e.lo = kLO;
+  e.hi = kHI;
   e.smem = smem_fn;
   e.prepare = prepare_fn;
   e.launch = launch_fn;

@@ -66,19 +66,23 @@ __device__ __forceinline__ T kummer_sum(T x) {
   return s;
 }
 
-template <int M, typename T, int G, int g>
+// Outputs of one order slice: Psi[beta] with LO <= |beta| <= HI, i.e. the
+// columns [B0, B1).  They need the jet orders LO .. HI + M only.
+template <int M, typename T, int LO, int HI>
 struct PairNear {
   static constexpr int K = n_moments(M);
   static constexpr int NB = n_beta(M);
-  static constexpr int NJ = jet_order(M);
+  static constexpr int NJ = HI + M;                // highest jet order of the slice
+  static constexpr int NLO = LO;                    // lowest jet order of the slice
   static constexpr int BMAX = bmax_of(M);
-  static constexpr int B0 = g * NB / G;
-  static constexpr int B1 = (g + 1) * NB / G;
+  static constexpr int B0 = tri(LO) - 1;
+  static constexpr int B1 = tri(HI + 1) - 1;
   static constexpr int NBL = B1 - B0;
   static constexpr int HN = NJ >= 2 ? NJ - 1 : 1;  // Hermite functions h_0..h_{NJ-2}
+  static_assert(LO >= 1 && HI <= bmax_of(M) && LO <= HI, "bad order slice");
 
   // Add one source's contribution (moments a[K], separation b in c = 1 units)
-  // to my slice acc[NBL] of Psi.  wmask = 0 removes the pair exactly (it is
+  // to this slice acc[NBL] of Psi.  wmask = 0 removes the pair exactly (it is
   // used for the self pair, whose separation the caller moves far away).
   __device__ __forceinline__ static void run(T b1, T b2, T l1, T l2, T wmask,
                                              const T (&a)[K], T (&acc)[NBL]) {
@@ -171,7 +175,7 @@ struct PairNear {
       hy[k] = fma(l2, hy[k + 1], hy[k]);
     });
 
-    static_for<1, NJ + 1>([&](auto nc) {
+    static_for<NLO, NJ + 1>([&](auto nc) {
       constexpr int n = decltype(nc)::value;
       const T f = T(((n - 1) & 1) ? -kInv4Pi : kInv4Pi) * wmask;
       const T w_r = wr[n - 1] * f;
@@ -223,5 +227,79 @@ struct PairNear {
     });
   }
 };
+
+// Far-field pair (x >= x_far(M) for every pair of the tile): the Gaussian part
+// of the jet is below FP32 rounding, psi is the point-vortex stream function
+// (1/4pi) ln|b|^2, and with u = 1/z its Cartesian jet is
+//   D_1^a D_2^{n-a} psi = Re((-i)^a omega_n),  omega_n = -(-i)^n (n-1)! u^n / (2 pi),
+// so the correlation collapses onto the source's complex multipoles
+//   A'_n = sum_{|m| = n} a_m (-i)^{m1 + n}                (written by prep)
+//   Y[nb] = sum_{n'=0}^{M} A'_{n'} rho_{n'+nb},  rho_n = (n-1)! u^n,
+//   Psi[beta] += -Re((-i)^{beta1 + |beta|} Y[|beta|]) / (2 pi).
+// Y is accumulated per target; fold_far adds it into the Psi slice.
+// Only the multipole orders LO <= nb <= HI of the slice are formed (Y[nb - LO]).
+template <int M, typename T, int LO, int HI>
+struct PairFar {
+  static constexpr int NJ = HI + M;
+  static constexpr int NY = HI - LO + 1;
+
+  __device__ __forceinline__ static void run(T b1, T b2, T l1, T l2, const T* af, T (&yr)[NY],
+                                             T (&yi)[NY]) {
+    const T inv = T(1) / (b1 * b1 + b2 * b2);
+    T ur = b1 * inv, ui = -b2 * inv;  // 1 / z_hi
+    // u = 1/(z_hi + l) = uh (1 - l uh) to first order in the low part l = l1 + i l2
+    const T tr = l1 * ur - l2 * ui, ti = l1 * ui + l2 * ur;
+    const T nr = ur - (ur * tr - ui * ti), ni = ui - (ur * ti + ui * tr);
+    ur = nr;
+    ui = ni;
+    T ar[M + 1], ai[M + 1];
+#pragma unroll
+    for (int n = 0; n <= M; ++n) {
+      ar[n] = af[2 * n];
+      ai[n] = af[2 * n + 1];
+    }
+    // rho_q = (q-1)! u^q, one order at a time; Y[nb] += A'_{q-nb} rho_q
+    T rr = ur, ri = ui;
+    static_for<1, NJ + 1>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      if constexpr (q > 1) {
+        const T pr = ur * rr - ui * ri;
+        const T pi = ur * ri + ui * rr;
+        rr = T(q - 1) * pr;
+        ri = T(q - 1) * pi;
+      }
+      static_for<0, M + 1>([&](auto nc) {
+        constexpr int n = decltype(nc)::value;
+        constexpr int nb = q - n;
+        if constexpr (nb >= LO && nb <= HI) {
+          yr[nb - LO] = fma(ar[n], rr, fma(-ai[n], ri, yr[nb - LO]));
+          yi[nb - LO] = fma(ar[n], ri, fma(ai[n], rr, yi[nb - LO]));
+        }
+      });
+    });
+  }
+};
+
+// Psi[beta] += -Re((-i)^{beta1+|beta|} Y[|beta|]) / (2 pi) over the slice's
+// outputs (acc indexed from column B0).
+template <int M, typename T, int LO, int HI>
+__device__ __forceinline__ void fold_far(const T (&yr)[HI - LO + 1], const T (&yi)[HI - LO + 1],
+                                         T* acc) {
+  using PN = PairNear<M, T, LO, HI>;
+  constexpr T s = T(1.0 / (2.0 * 3.14159265358979323846));
+  static_for<LO, HI + 1>([&](auto nbc) {
+    constexpr int nb = decltype(nbc)::value;
+    static_for<0, nb + 1>([&](auto b2c) {
+      constexpr int bb2 = decltype(b2c)::value;
+      constexpr int bb1 = nb - bb2;
+      constexpr int col = bcol(bb1, bb2) - PN::B0;
+      constexpr int r = (bb1 + nb) & 3;
+      if constexpr (r == 0) acc[col] -= s * yr[nb - LO];
+      if constexpr (r == 1) acc[col] -= s * yi[nb - LO];
+      if constexpr (r == 2) acc[col] += s * yr[nb - LO];
+      if constexpr (r == 3) acc[col] += s * yi[nb - LO];
+    });
+  });
+}
 
 }  // namespace mmvm

@@ -1,7 +1,22 @@
-// Launch wrapper of the all-pairs kernel: one thread per (target, output
-// slice), source records staged through shared memory in tiles of S, FP32
-// partial sums carried across tiles as (hi, lo) float pairs (TwoSum), and the
+// Launch wrapper of the all-pairs kernel: one thread per target, source
+// records staged through shared memory in tiles of S = kGroup, FP32 partial
+// sums carried across tiles as (hi, lo) float pairs (TwoSum), and the
 // per-(source chunk, target) result written as FP64.
+//
+// One kernel computes one order slice of the outputs, LO <= |beta| <= HI (a
+// variant launches its slices one after another).  Slicing keeps the fully
+// unrolled per-pair code of each kernel short enough for the instruction
+// cache and needs only jet orders LO .. HI + M in each slice.
+// Other variant parameters (chosen per order by the autotuner):
+//   TPC   targets per CTA (a multiple of 32, so each warp is one group);
+//   MINB  CTAs per SM the register budget must allow;
+//   SYNC  a CTA barrier after every source, which keeps the warps of a CTA on
+//         the same stretch of code so they share instruction-cache lines.
+// FP32 runs two passes over the chunk's source tiles: first the tiles whose
+// bounding box is beyond x_far(M) of the warp's target group (point-vortex
+// multipoles, PairFar), then the others (full jet, PairNear); the two paths
+// never hold registers at the same time.  Every barrier is one instruction
+// executed by the whole CTA.
 #pragma once
 
 #include "common.cuh"
@@ -9,124 +24,108 @@
 
 namespace mmvm {
 
-struct PairLaunch {
-  int targets_per_cta;  // TPC
-  int tile;             // S sources per shared-memory tile
-  int chunks;           // source chunks (grid.y)
-};
-
-// Layout of `partial`: [chunk][beta column][target] FP64 (coalesced writes).
-// acc points at a register array of at least NBL entries; every index used
-// below is a compile-time constant after inlining, so it stays in registers.
-
-// Accumulate `cnt` staged sources into this slice's registers, then (FP32)
-// fold the tile's sums into the shared-memory (hi, lo) pairs.
-template <int M, typename T, int G, int g, int TPC>
-__device__ __forceinline__ void pair_tile(const T* tile, int cnt, int t0, int j, T tz1, T tz2,
-                                          T tl1, T tl2, T* acc, float* acc_hi, float* acc_lo,
-                                          int slot) {
-  using PN = PairNear<M, T, G, g>;
+// One near-field source.  acc points at the register array of the slice;
+// every index used is a compile-time constant after inlining.
+template <int M, typename T, int LO, int HI>
+__device__ __forceinline__ void near_source(const T* r, int src, int j, T tz1, T tz2, T tl1,
+                                            T tl2, T* acc) {
+  using PN = PairNear<M, T, LO, HI>;
   constexpr int K = n_moments(M);
-  constexpr int NBL = PN::NBL;
-  constexpr int R = rec_len<T>(M);
   constexpr int HDR = Rec<T>::HDR;
-  constexpr bool f32 = std::is_same<T, float>::value;
-  T (&accr)[NBL] = *reinterpret_cast<T(*)[NBL]>(acc);
-#pragma unroll 1
-  for (int s = 0; s < cnt; ++s) {
-    const T* r = tile + s * R;
-    T a[K];
+  T (&accr)[PN::NBL] = *reinterpret_cast<T(*)[PN::NBL]>(acc);
+  T a[K];
 #pragma unroll
-    for (int m = 0; m < K; ++m) a[m] = r[HDR + m];
-    T b1, b2, l1 = T(0), l2 = T(0);
-    if constexpr (f32) {
-      // b = (hi difference) + (lo difference) as an exact (hi, lo) pair
-      const T d1 = tz1 - r[0], e1 = tl1 - r[2];
-      const T d2 = tz2 - r[1], e2 = tl2 - r[3];
-      b1 = d1 + e1;
-      b2 = d2 + e2;
-      const T v1 = b1 - d1, v2 = b2 - d2;
-      l1 = (d1 - (b1 - v1)) + (e1 - v1);
-      l2 = (d2 - (b2 - v2)) + (e2 - v2);
-    } else {
-      b1 = tz1 - r[0];
-      b2 = tz2 - r[1];
-    }
-    T wm = T(1);
-    if (t0 + s == j) {  // self pair: excluded here, added exactly by the finish
-      b1 = T(1e15);
-      b2 = T(0);
-      l1 = T(0);
-      l2 = T(0);
-      wm = T(0);
-    }
-    PN::run(b1, b2, l1, l2, wm, a, accr);
+  for (int m = 0; m < K; ++m) a[m] = r[HDR + m];
+  T b1, b2, l1 = T(0), l2 = T(0);
+  if constexpr (std::is_same<T, float>::value) {
+    // b = (hi difference) + (lo difference) as an exact (hi, lo) pair
+    const T d1 = tz1 - r[0], e1 = tl1 - r[2];
+    const T d2 = tz2 - r[1], e2 = tl2 - r[3];
+    b1 = d1 + e1;
+    b2 = d2 + e2;
+    const T v1 = b1 - d1, v2 = b2 - d2;
+    l1 = (d1 - (b1 - v1)) + (e1 - v1);
+    l2 = (d2 - (b2 - v2)) + (e2 - v2);
+  } else {
+    b1 = tz1 - r[0];
+    b2 = tz2 - r[1];
   }
-  if constexpr (f32) {
+  T wm = T(1);
+  if (src == j) {  // self pair: excluded here, added exactly by the finish
+    b1 = T(1e15);
+    b2 = T(0);
+    l1 = T(0);
+    l2 = T(0);
+    wm = T(0);
+  }
+  PN::run(b1, b2, l1, l2, wm, a, accr);
+}
+
+// Fold FP32 register sums into this thread's shared-memory (hi, lo) pairs.
+template <int NBL, int TPC>
+__device__ __forceinline__ void flush_sums(float* acc, float* acc_hi, float* acc_lo, int slot) {
 #pragma unroll
-    for (int b = 0; b < NBL; ++b) {
-      const int idx = (PN::B0 + b) * TPC + slot;
-      const float hi = acc_hi[idx];
-      const float sum = hi + accr[b];
-      const float bp = sum - hi;
-      const float err = (hi - (sum - bp)) + (accr[b] - bp);
-      acc_hi[idx] = sum;
-      acc_lo[idx] += err;
-      accr[b] = 0.f;
-    }
+  for (int b = 0; b < NBL; ++b) {
+    const int idx = b * TPC + slot;
+    const float hi = acc_hi[idx];
+    const float sum = hi + acc[b];
+    const float bp = sum - hi;
+    const float err = (hi - (sum - bp)) + (acc[b] - bp);
+    acc_hi[idx] = sum;
+    acc_lo[idx] += err;
+    acc[b] = 0.f;
   }
 }
 
-// Warp-uniform dispatch to output slice gg (forced inline, no lambda).
-template <int M, typename T, int G, int TPC, int gg>
-__device__ __forceinline__ void pair_tile_dispatch(int g, const T* tile, int cnt, int t0, int j,
-                                                   T tz1, T tz2, T tl1, T tl2, T* acc,
-                                                   float* acc_hi, float* acc_lo, int slot) {
-  if (g == gg) {
-    pair_tile<M, T, G, gg, TPC>(tile, cnt, t0, j, tz1, tz2, tl1, tl2, acc, acc_hi, acc_lo, slot);
-  } else if constexpr (gg + 1 < G) {
-    pair_tile_dispatch<M, T, G, TPC, gg + 1>(g, tile, cnt, t0, j, tz1, tz2, tl1, tl2, acc,
-                                             acc_hi, acc_lo, slot);
-  }
+// One far-field source (FP32): multipole sums of the tile in yr/yi.
+template <int M, int LO, int HI>
+__device__ __forceinline__ void far_source(const float* r, float tz1, float tz2, float tl1,
+                                           float tl2, float (&yr)[HI - LO + 1],
+                                           float (&yi)[HI - LO + 1]) {
+  constexpr int K = n_moments(M);
+  constexpr int HDR = Rec<float>::HDR;
+  const float d1 = tz1 - r[0], e1 = tl1 - r[2];
+  const float d2 = tz2 - r[1], e2 = tl2 - r[3];
+  const float b1 = d1 + e1, b2 = d2 + e2;
+  const float v1 = b1 - d1, v2 = b2 - d2;
+  const float l1 = (d1 - (b1 - v1)) + (e1 - v1);
+  const float l2 = (d2 - (b2 - v2)) + (e2 - v2);
+  PairFar<M, float, LO, HI>::run(b1, b2, l1, l2, r + HDR + K, yr, yi);
 }
 
-template <int M, typename T, int G, int TPC, int gg>
-__device__ __forceinline__ void pair_store_dispatch(int g, int n, int j, const T* acc,
-                                                    const float* acc_hi, const float* acc_lo,
-                                                    int slot, double* __restrict__ out) {
-  using PN = PairNear<M, T, G, gg>;
-  if (g == gg) {
-#pragma unroll
-    for (int b = 0; b < PN::NBL; ++b) {
-      double v;
-      if constexpr (std::is_same<T, float>::value) {
-        const int idx = (PN::B0 + b) * TPC + slot;
-        v = (double)acc_hi[idx] + (double)acc_lo[idx];
-      } else {
-        v = acc[b];
-      }
-      out[(size_t)(PN::B0 + b) * n + j] = v;
-    }
-  } else if constexpr (gg + 1 < G) {
-    pair_store_dispatch<M, T, G, TPC, gg + 1>(g, n, j, acc, acc_hi, acc_lo, slot, out);
-  }
+// Does this warp's target group see source group sg only beyond x_far(M)?
+template <int M>
+__device__ __forceinline__ bool tile_is_far(const float4* __restrict__ gbox, int tgroup,
+                                            int sg) {
+  const float4 sb = gbox[sg];
+  const float4 tb = gbox[tgroup];
+  const float dx = fmaxf(0.f, fmaxf(tb.x - sb.y, sb.x - tb.y));
+  const float dy = fmaxf(0.f, fmaxf(tb.z - sb.w, sb.z - tb.w));
+  return dx * dx + dy * dy >= x_far(M);
 }
 
-template <int M, typename T, int G, int TPC>
-__global__ void __launch_bounds__(TPC * G) pair_kernel(const T* __restrict__ rec, int n,
-                                                       int chunk_len, int S,
-                                                       double* __restrict__ partial) {
+// gbox: per group of kGroup consecutive records, (min z1, max z1, min z2,
+// max z2) of the hi parts; null disables the far-field path (FP64 always).
+// Layout of `partial`: [chunk][beta column][target] FP64 (coalesced writes);
+// this kernel writes the columns of its slice only.  counts (nullable):
+// cumulative (near, far) pair counts, added by the first slice only.
+template <int M, typename T, int LO, int HI, int TPC, int MINB, bool SYNC>
+__global__ void __launch_bounds__(TPC, MINB)
+    pair_kernel(const T* __restrict__ rec, int n, int chunk_len, int S,
+                const float4* __restrict__ gbox, double* __restrict__ partial,
+                unsigned long long* __restrict__ counts) {
+  using PN = PairNear<M, T, LO, HI>;
   constexpr int R = rec_len<T>(M);
   constexpr int NB = n_beta(M);
-  constexpr int NBLMAX = (NB + G - 1) / G;
+  constexpr int NBL = PN::NBL;
+  constexpr int NY = HI - LO + 1;
+  constexpr bool f32 = std::is_same<T, float>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
   float* acc_hi = reinterpret_cast<float*>(tile + (size_t)S * R);
-  float* acc_lo = acc_hi + NB * TPC;
+  float* acc_lo = acc_hi + NBL * TPC;
   const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  const int g = warp % G;
-  const int slot = (warp / G) * 32 + lane;
+  const int slot = threadIdx.x;
   const int j = blockIdx.x * TPC + slot;
   const int c0 = blockIdx.y * chunk_len;
   const int c1 = min(n, c0 + chunk_len);
@@ -135,7 +134,7 @@ __global__ void __launch_bounds__(TPC * G) pair_kernel(const T* __restrict__ rec
     const T* r = rec + (size_t)j * R;
     tz1 = r[0];
     tz2 = r[1];
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (f32) {
       tl1 = r[2];
       tl2 = r[3];
     }
@@ -143,52 +142,113 @@ __global__ void __launch_bounds__(TPC * G) pair_kernel(const T* __restrict__ rec
     tz1 = T(3e15);
     tz2 = T(3e15);
   }
-  T acc[NBLMAX];
+  T acc[NBL];
 #pragma unroll
-  for (int b = 0; b < NBLMAX; ++b) acc[b] = T(0);
-  if constexpr (std::is_same<T, float>::value) {
-    for (int i = threadIdx.x; i < 2 * NB * TPC; i += blockDim.x) acc_hi[i] = 0.f;
+  for (int b = 0; b < NBL; ++b) acc[b] = T(0);
+  if constexpr (f32) {
+    for (int i = threadIdx.x; i < 2 * NBL * TPC; i += blockDim.x) acc_hi[i] = 0.f;
   }
+  const bool use_far = f32 && gbox != nullptr;
+  unsigned n_near = 0, n_far = 0;  // pairs of this thread's target on each path
+  // this warp's 32 targets form one group; a warp wholly past n does no work
+  // (but still takes part in every barrier)
+  const int wfirst = blockIdx.x * TPC + warp * 32;
+  const bool warp_valid = wfirst < n;
+  const int tgroup = wfirst / kGroup;
+  auto load_tile = [&](int t0, int cnt) {
+    // cooperative 16-byte copy of cnt records into the tile
+    const int nvec = cnt * R * (int)sizeof(T) / 16;
+    const int4* src = reinterpret_cast<const int4*>(rec + (size_t)t0 * R);
+    int4* dst = reinterpret_cast<int4*>(tile);
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
+  };
+  if constexpr (f32) {
+    if (use_far) {
+      // pass 1: far tiles (tiles start at multiples of kGroup: chunk_len is a
+      // multiple of S = kGroup)
+#pragma unroll 1
+      for (int t0 = c0; t0 < c1; t0 += S) {
+        const int cnt = min(S, c1 - t0);
+        const bool far = warp_valid && tile_is_far<M>(gbox, tgroup, t0 / kGroup);
+        if (far && j < n) n_far += cnt;
+        if (__syncthreads_or(far)) {
+          load_tile(t0, cnt);
+          __syncthreads();
+          float yr[NY], yi[NY];  // multipole sums of this tile
+#pragma unroll
+          for (int b = 0; b < NY; ++b) {
+            yr[b] = 0.f;
+            yi[b] = 0.f;
+          }
+#pragma unroll 1
+          for (int s = 0; s < cnt; ++s) {
+            if (far)
+              far_source<M, LO, HI>(reinterpret_cast<const float*>(tile) + s * R, tz1, tz2, tl1,
+                                    tl2, yr, yi);
+            if constexpr (SYNC) __syncthreads();
+          }
+          if (far) {
+            float tmp[NBL];
+#pragma unroll
+            for (int b = 0; b < NBL; ++b) tmp[b] = 0.f;
+            fold_far<M, float, LO, HI>(yr, yi, tmp);
+            flush_sums<NBL, TPC>(tmp, acc_hi, acc_lo, slot);
+          }
+        }
+      }
+    }
+  }
+  // pass 2: near tiles (every tile when the far field is off)
 #pragma unroll 1
   for (int t0 = c0; t0 < c1; t0 += S) {
     const int cnt = min(S, c1 - t0);
-    __syncthreads();
-    {
-      // cooperative 16-byte copy of cnt records into the tile
-      const int nvec = cnt * R * (int)sizeof(T) / 16;
-      const int4* src = reinterpret_cast<const int4*>(rec + (size_t)t0 * R);
-      int4* dst = reinterpret_cast<int4*>(tile);
-      for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
+    bool near = warp_valid;
+    if constexpr (f32) {
+      if (use_far && warp_valid) near = !tile_is_far<M>(gbox, tgroup, t0 / kGroup);
     }
-    __syncthreads();
-    pair_tile_dispatch<M, T, G, TPC, 0>(g, tile, cnt, t0, j, tz1, tz2, tl1, tl2, acc, acc_hi,
-                                        acc_lo, slot);
+    if (near && j < n) n_near += cnt;
+    if (__syncthreads_or(near)) {
+      load_tile(t0, cnt);
+      __syncthreads();
+#pragma unroll 1
+      for (int s = 0; s < cnt; ++s) {
+        if (near) near_source<M, T, LO, HI>(tile + s * R, t0 + s, j, tz1, tz2, tl1, tl2, acc);
+        if constexpr (SYNC) __syncthreads();
+      }
+      if constexpr (f32) {
+        if (near) flush_sums<NBL, TPC>(acc, acc_hi, acc_lo, slot);
+      }
+    }
+  }
+  if (LO == 1 && counts != nullptr) {
+    const unsigned wn = __reduce_add_sync(0xffffffffu, n_near);
+    const unsigned wf = __reduce_add_sync(0xffffffffu, n_far);
+    if ((threadIdx.x & 31) == 0) {
+      if (wn) atomicAdd(counts, (unsigned long long)wn);
+      if (wf) atomicAdd(counts + 1, (unsigned long long)wf);
+    }
   }
   if (j < n) {
-    pair_store_dispatch<M, T, G, TPC, 0>(g, n, j, acc, acc_hi, acc_lo, slot,
-                                         partial + (size_t)blockIdx.y * NB * n);
+    double* out = partial + (size_t)blockIdx.y * NB * n + (size_t)PN::B0 * n + j;
+#pragma unroll
+    for (int b = 0; b < NBL; ++b) {
+      double v;
+      if constexpr (f32) {
+        v = (double)acc_hi[b * TPC + slot] + (double)acc_lo[b * TPC + slot];
+      } else {
+        v = acc[b];
+      }
+      out[(size_t)b * n] = v;
+    }
   }
 }
 
-template <int M, typename T, int G, int TPC>
-size_t pair_smem_bytes(int S) {
+template <int M, typename T, int LO, int HI, int TPC>
+size_t pair_smem_bytes(int S) {  // shared memory of one CTA
   size_t b = (size_t)S * rec_len<T>(M) * sizeof(T);
-  if (std::is_same<T, float>::value) b += 2 * (size_t)n_beta(M) * TPC * sizeof(float);
+  if (std::is_same<T, float>::value)
+    b += 2 * (size_t)PairNear<M, T, LO, HI>::NBL * TPC * sizeof(float);
   return b;
-}
-
-template <int M, typename T, int G, int TPC>
-cudaError_t launch_pair_t(const T* rec, int n, int chunks, int S, double* partial,
-                          cudaStream_t st) {
-  const int chunk_len = (n + chunks - 1) / chunks;
-  const size_t smem = pair_smem_bytes<M, T, G, TPC>(S);
-  auto kern = pair_kernel<M, T, G, TPC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((n + TPC - 1) / TPC, chunks);
-  kern<<<grid, TPC * G, smem, st>>>(rec, n, chunk_len, S, partial);
-  return cudaGetLastError();
 }
 
 }  // namespace mmvm

@@ -1,26 +1,52 @@
-// Registry of compiled all-pairs kernel variants, one per (order, precision).
+// Registry of compiled all-pairs kernel variants, per (order, precision).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "pair_variants.h"
+
 namespace mmvm {
 
-struct PairEntry {
-  int M = -1;
-  int precision = 0;      // 0: FP64, 1: FP32
-  int tpc = 0;            // targets per CTA
-  int g = 1;              // threads (output slices) per target
-  int rec_len = 0;        // record length in elements
-  int elem_bytes = 0;     // sizeof(T)
+// One order slice of a variant (one kernel).
+struct SliceEntry {
+  int lo = 0, hi = 0;
   size_t (*smem)(int S) = nullptr;
-  cudaError_t (*prepare)(int S) = nullptr;   // set the dynamic shared-memory limit
-  cudaError_t (*launch)(const void* rec, int n, int chunks, int S, double* partial,
-                        cudaStream_t st) = nullptr;
+  cudaError_t (*prepare)(int S) = nullptr;  // set the dynamic shared-memory limit
+  cudaError_t (*launch)(const void* rec, int n, int chunk_len, int gy, int S, const void* gbox,
+                        double* partial, unsigned long long* counts, cudaStream_t st) = nullptr;
   cudaError_t (*occupancy)(int S, int* blocks_per_sm) = nullptr;
 };
 
-// nullptr-like entry (M == -1) if the variant is not compiled.
-PairEntry pair_entry(int M, int precision);
+struct PairEntry {
+  int M = -1;               // -1: no such variant
+  int precision = 0;        // 0: FP64, 1: FP32
+  int variant = 0;
+  int tpc = 0;              // targets per CTA
+  int minb = 1;             // CTAs per SM the register budget allows
+  int sync = 0;             // barrier after every source
+  int nslices = 0;
+  SliceEntry slices[kMaxSlices];
+  int rec_len = 0;          // record length in elements
+  int elem_bytes = 0;       // sizeof(T)
+};
+
+// Number of compiled variants of (M, precision); 0 if none.
+int pair_variant_count(int M, int precision);
+// Variant v (an entry with M == -1 if it does not exist).
+PairEntry pair_entry(int M, int precision, int v);
+// Set the shared-memory limit of every slice kernel.
+cudaError_t pair_prepare(const PairEntry& e, int S);
+// CTAs per SM of the slice kernels (the smallest), 0 on error.
+int pair_occupancy(const PairEntry& e, int S);
+// Launch every slice.  gbox: float4 per group of kGroup records (null: every
+// pair takes the full jet); S must equal kGroup.  Sources are split into
+// `chunks` chunks of a multiple of S; `partial` holds min(chunks, grid_y_limit)
+// chunks (grid_y_limit > 0 launches only the first grid_y_limit chunks, used
+// when timing variants; 0 launches all of them).  counts (nullable) receives
+// the cumulative (near, far) pair counts.
+cudaError_t pair_launch(const PairEntry& e, const void* rec, int n, int chunks, int S,
+                        const void* gbox, double* partial, int grid_y_limit, cudaStream_t st,
+                        unsigned long long* counts = nullptr);
 
 }  // namespace mmvm

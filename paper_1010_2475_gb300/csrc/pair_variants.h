@@ -1,0 +1,72 @@
+// Compiled variants of the all-pairs kernel per (order M, precision).  A
+// variant is a list of order slices [lo, hi] of the outputs (one kernel each,
+// launched in turn) plus the CTA shape: TPC targets per CTA, MINB CTAs per SM
+// the register budget must allow, SYNC barrier after every source.  The
+// autotuner times the variants on the first state of each size and keeps the
+// fastest.  FP32 keeps 2 x (outputs of the slice) x TPC floats of (hi, lo)
+// sums in shared memory, which bounds TPC for wide slices.
+#pragma once
+
+namespace mmvm {
+
+struct SliceSpec {
+  int lo, hi;
+};
+
+constexpr int kMaxVariants = 4;
+constexpr int kMaxSlices = 4;
+
+struct VariantSpec {
+  int nslices;
+  SliceSpec s[kMaxSlices];
+  int TPC, MINB, SYNC;
+};
+
+constexpr int n_variants(int M, int prec) {
+  if (prec == 0) return 1;
+  return M <= 3 ? 1 : (M == 7 ? 2 : (M == 6 ? 4 : 3));
+}
+
+constexpr VariantSpec variant_spec(int M, int prec, int v) {
+  if (prec == 0) {  // FP64: narrow slices keep the FP64 accumulators in registers
+    switch (M) {
+      case 0: return {1, {{1, 1}}, 64, 1, 0};
+      case 1: return {1, {{1, 2}}, 64, 1, 0};
+      case 2: return {1, {{1, 4}}, 64, 1, 0};
+      case 3: return {1, {{1, 6}}, 64, 1, 0};
+      case 4: return {2, {{1, 5}, {6, 8}}, 64, 1, 0};
+      case 5: return {2, {{1, 6}, {7, 10}}, 64, 1, 0};
+      case 6: return {3, {{1, 7}, {8, 10}, {11, 12}}, 64, 1, 0};
+      case 7: return {4, {{1, 7}, {8, 10}, {11, 12}, {13, 14}}, 64, 1, 0};
+      default: return {4, {{1, 8}, {9, 11}, {12, 14}, {15, 16}}, 64, 1, 0};
+    }
+  }
+  switch (M) {
+    case 0: return {1, {{1, 1}}, 128, 3, 0};
+    case 1: return {1, {{1, 2}}, 128, 3, 0};
+    case 2: return {1, {{1, 4}}, 128, 3, 0};
+    case 3: return {1, {{1, 6}}, 128, 3, 0};
+    case 4:
+      return v == 0 ? VariantSpec{1, {{1, 8}}, 128, 3, 0}
+           : v == 1 ? VariantSpec{1, {{1, 8}}, 256, 1, 1}
+                    : VariantSpec{2, {{1, 5}, {6, 8}}, 128, 2, 1};
+    case 5:
+      return v == 0 ? VariantSpec{1, {{1, 10}}, 256, 1, 1}
+           : v == 1 ? VariantSpec{2, {{1, 7}, {8, 10}}, 128, 2, 1}
+                    : VariantSpec{2, {{1, 7}, {8, 10}}, 256, 1, 1};
+    case 6:
+      return v == 0 ? VariantSpec{1, {{1, 12}}, 256, 1, 1}
+           : v == 1 ? VariantSpec{2, {{1, 8}, {9, 12}}, 128, 2, 1}
+           : v == 2 ? VariantSpec{3, {{1, 6}, {7, 9}, {10, 12}}, 128, 2, 1}
+                    : VariantSpec{2, {{1, 8}, {9, 12}}, 256, 1, 1};
+    case 7:
+      return v == 0 ? VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 1}
+                    : VariantSpec{3, {{1, 7}, {8, 11}, {12, 14}}, 128, 2, 1};
+    default:
+      return v == 0 ? VariantSpec{3, {{1, 8}, {9, 12}, {13, 16}}, 128, 2, 1}
+           : v == 1 ? VariantSpec{4, {{1, 8}, {9, 11}, {12, 14}, {15, 16}}, 128, 2, 1}
+                    : VariantSpec{4, {{1, 8}, {9, 11}, {12, 14}, {15, 16}}, 256, 1, 1};
+  }
+}
+
+}  // namespace mmvm

@@ -21,39 +21,73 @@ __device__ __forceinline__ double stage_c(const double* t_dev, const double* dt_
   return 2.0 * (lam0sq + four_nu * t);
 }
 
+// Sorted position p holds particle perm[p] (perm == null: identity).  FP32
+// records also get the far-field multipoles A'_n = sum_{|m|=n} a_m (-i)^{m1+n}
+// and every warp (kGroup consecutive positions) writes the bounding box of its
+// hi-part centres to gbox (if given).
 template <typename T>
-__global__ void prep_kernel(int n, int M, int K, int R, const double* __restrict__ x,
-                            const double* __restrict__ mom, const double* t_dev,
-                            const double* dt_dev, double cs, double lam0sq, double four_nu,
-                            T* __restrict__ rec) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const double c = stage_c(t_dev, dt_dev, cs, lam0sq, four_nu);
-  const double irc = 1.0 / sqrt(c);
-  T* r = rec + (size_t)j * R;
-  const double z1 = x[2 * j] * irc;
-  const double z2 = x[2 * j + 1] * irc;
-  int h;
-  if constexpr (sizeof(T) == 4) {
-    const float h1 = (float)z1, h2 = (float)z2;
-    r[0] = h1;
-    r[1] = h2;
-    r[2] = (float)(z1 - (double)h1);
-    r[3] = (float)(z2 - (double)h2);
-    h = 4;
-  } else {
-    r[0] = (T)z1;
-    r[1] = (T)z2;
-    h = 2;
+__global__ void prep_kernel(int n, int M, int K, int R, const int* __restrict__ perm,
+                            const double* __restrict__ x, const double* __restrict__ mom,
+                            const double* t_dev, const double* dt_dev, double cs, double lam0sq,
+                            double four_nu, T* __restrict__ rec, float4* __restrict__ gbox) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = p < n;
+  float lo1 = 3.4e38f, hi1 = -3.4e38f, lo2 = 3.4e38f, hi2 = -3.4e38f;
+  if (valid) {
+    const int j = perm ? perm[p] : p;
+    const double c = stage_c(t_dev, dt_dev, cs, lam0sq, four_nu);
+    const double irc = 1.0 / sqrt(c);
+    T* r = rec + (size_t)p * R;
+    const double z1 = x[2 * j] * irc;
+    const double z2 = x[2 * j + 1] * irc;
+    int h;
+    if constexpr (sizeof(T) == 4) {
+      const float h1 = (float)z1, h2 = (float)z2;
+      r[0] = h1;
+      r[1] = h2;
+      r[2] = (float)(z1 - (double)h1);
+      r[3] = (float)(z2 - (double)h2);
+      h = 4;
+      lo1 = hi1 = h1;
+      lo2 = hi2 = h2;
+    } else {
+      r[0] = (T)z1;
+      r[1] = (T)z2;
+      h = 2;
+    }
+    const double* mj = mom + (size_t)j * K;
+    double sc = 1.0;
+    int col = 0;
+    for (int s = 0; s <= M; ++s) {
+      double fr = 0.0, fi = 0.0;  // A'_s
+      for (int k2 = 0; k2 <= s; ++k2, ++col) {
+        const double a = mj[col] * sc;
+        r[h + col] = (T)a;
+        switch ((s - k2 + s) & 3) {  // (-i)^{m1 + s}, m1 = s - k2
+          case 0: fr += a; break;
+          case 1: fi -= a; break;
+          case 2: fr -= a; break;
+          default: fi += a; break;
+        }
+      }
+      if constexpr (sizeof(T) == 4) {
+        r[h + K + 2 * s] = (T)fr;
+        r[h + K + 2 * s + 1] = (T)fi;
+      }
+      sc *= irc;
+    }
+    for (int q = h + K + rec_far<T>(M); q < R; ++q) r[q] = T(0);
   }
-  const double* mj = mom + (size_t)j * K;
-  double sc = 1.0;
-  int col = 0;
-  for (int s = 0; s <= M; ++s) {
-    for (int k2 = 0; k2 <= s; ++k2, ++col) r[h + col] = (T)(mj[col] * sc);
-    sc *= irc;
+  if (gbox) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+      hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+      lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+      hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+    }
+    if ((threadIdx.x & 31) == 0 && valid) gbox[p / kGroup] = make_float4(lo1, hi1, lo2, hi2);
   }
-  for (int p = h + K; p < R; ++p) r[p] = T(0);
 }
 
 // Shared-memory layout per block: for each of TB targets, Psi[NB], a[K], X[2],
@@ -67,7 +101,7 @@ __global__ void finish_kernel(FinishArgs A) {
   double* X = at + TB * K;                // TB * 2
   double* m00s = X + TB * 2;              // TB
   double* cpow = m00s + TB;               // c^{-s/2}, s = 0..2M+2
-  const int j0 = blockIdx.x * TB;
+  const int j0 = blockIdx.x * TB;  // sorted positions; particle = perm[position]
   const double c = stage_c(A.t_dev, A.dt_dev, A.cs, A.lam0sq, A.four_nu);
   for (int s = threadIdx.x; s <= 2 * M + 2; s += blockDim.x) cpow[s] = pow(c, -0.5 * s);
   __syncthreads();
@@ -81,12 +115,13 @@ __global__ void finish_kernel(FinishArgs A) {
     psi[idx] = v;
   }
   for (int idx = threadIdx.x; idx < TB * K; idx += blockDim.x) {
-    const int tt = idx / K, m = idx % K, j = j0 + tt;
+    const int tt = idx / K, m = idx % K, p = j0 + tt;
     int s = 0;
     while ((s + 1) * (s + 2) / 2 <= m) ++s;  // total order of column m
-    const double mv = (j < A.n) ? A.Min[(size_t)j * K + m] : 0.0;
+    const int j = p < A.n ? (A.perm ? A.perm[p] : p) : 0;
+    const double mv = (p < A.n) ? A.Min[(size_t)j * K + m] : 0.0;
     at[idx] = mv * cpow[s];
-    if (m == 0) m00s[tt] = (j < A.n) ? mv : 1.0;
+    if (m == 0) m00s[tt] = (p < A.n) ? mv : 1.0;
   }
   __syncthreads();
   // 2. centroid sums X_c = sum_m (-1)^{|m|} a_m What_c[m], What_1[m] = -Psi[m+e2],
@@ -127,8 +162,9 @@ __global__ void finish_kernel(FinishArgs A) {
   __syncthreads();
   // 4. moment equation and centroid velocity per (target, k)
   for (int idx = threadIdx.x; idx < TB * K; idx += blockDim.x) {
-    const int tt = idx / K, k = idx % K, j = j0 + tt;
-    if (j >= A.n) continue;
+    const int tt = idx / K, k = idx % K, p = j0 + tt;
+    if (p >= A.n) continue;
+    const int j = A.perm ? A.perm[p] : p;
     int kn = 0;
     while ((kn + 1) * (kn + 2) / 2 <= k) ++kn;
     const int k2 = k - tri(kn), k1 = kn - k2;
@@ -155,8 +191,9 @@ __global__ void finish_kernel(FinishArgs A) {
   }
   // 5. centroid velocity xdot_c = c^{-1/2} X_c / M_00 and its stage update
   for (int idx = threadIdx.x; idx < TB * 2; idx += blockDim.x) {
-    const int tt = idx >> 1, comp = idx & 1, j = j0 + tt;
-    if (j >= A.n) continue;
+    const int tt = idx >> 1, comp = idx & 1, p = j0 + tt;
+    if (p >= A.n) continue;
+    const int j = A.perm ? A.perm[p] : p;
     const double dx = X[idx] * cpow[1] / m00s[tt];
     const size_t ox = (size_t)j * 2 + comp;
     if (A.mode == 0) {
@@ -188,17 +225,19 @@ __global__ void scan_state_kernel(int n, int K, const double* __restrict__ x,
   if (mom[(size_t)j * K] == 0.0) atomicOr(flags + 1, 1);
 }
 
-cudaError_t launch_prep(int precision, int n, int M, const double* x, const double* mom,
-                        const double* t_dev, const double* dt_dev, double cs, double lam0sq,
-                        double four_nu, void* rec, cudaStream_t st) {
+cudaError_t launch_prep(int precision, int n, int M, const int* perm, const double* x,
+                        const double* mom, const double* t_dev, const double* dt_dev, double cs,
+                        double lam0sq, double four_nu, void* rec, void* gbox, cudaStream_t st) {
   const int K = n_moments(M);
   const int threads = 128, blocks = (n + threads - 1) / threads;
   if (precision == 1) {
-    prep_kernel<float><<<blocks, threads, 0, st>>>(n, M, K, rec_len<float>(M), x, mom, t_dev,
-                                                   dt_dev, cs, lam0sq, four_nu, (float*)rec);
+    prep_kernel<float><<<blocks, threads, 0, st>>>(n, M, K, rec_len<float>(M), perm, x, mom,
+                                                   t_dev, dt_dev, cs, lam0sq, four_nu,
+                                                   (float*)rec, (float4*)gbox);
   } else {
-    prep_kernel<double><<<blocks, threads, 0, st>>>(n, M, K, rec_len<double>(M), x, mom, t_dev,
-                                                    dt_dev, cs, lam0sq, four_nu, (double*)rec);
+    prep_kernel<double><<<blocks, threads, 0, st>>>(n, M, K, rec_len<double>(M), perm, x, mom,
+                                                    t_dev, dt_dev, cs, lam0sq, four_nu,
+                                                    (double*)rec, nullptr);
   }
   return cudaGetLastError();
 }

@@ -9,7 +9,8 @@ struct FinishArgs {
   int n = 0, M = 0, K = 0, NB = 0;
   int nchunks = 0;                  // number of pair partials (0: single particle)
   int targets_per_block = 1;
-  const double* partial = nullptr;  // [nchunks][NB][n]
+  const double* partial = nullptr;  // [nchunks][NB][n] by sorted position
+  const int* perm = nullptr;        // sorted position -> particle (null: identity)
   const double* Min = nullptr;      // stage moments (n x K)
   const int* k_off = nullptr;       // finish tables (tables.h)
   const int* e_l = nullptr;
@@ -31,9 +32,14 @@ struct FinishArgs {
   double* sum_M = nullptr;
 };
 
-cudaError_t launch_prep(int precision, int n, int M, const double* x, const double* mom,
-                        const double* t_dev, const double* dt_dev, double cs, double lam0sq,
-                        double four_nu, void* rec, cudaStream_t st);
+cudaError_t launch_prep(int precision, int n, int M, const int* perm, const double* x,
+                        const double* mom, const double* t_dev, const double* dt_dev, double cs,
+                        double lam0sq, double four_nu, void* rec, void* gbox, cudaStream_t st);
+// Spatial order: perm[p] = particle at sorted position p (Morton order of the
+// centres, ties by index).  temp_bytes() sizes the scratch for n particles.
+size_t spatial_order_temp_bytes(int n);
+cudaError_t launch_spatial_order(int n, const double* x, void* temp, size_t temp_bytes,
+                                 int* perm, cudaStream_t st);
 cudaError_t launch_finish(const FinishArgs& A, cudaStream_t st);
 cudaError_t launch_advance_time(double* t_dev, const double* dt_dev, cudaStream_t st);
 cudaError_t launch_scan(int n, int K, const double* x, const double* mom, int* flags,

@@ -188,3 +188,48 @@ def test_error_codes(mm):
         with pytest.raises(mm.MMVMError) as ei:
             ctx.set_state(np.zeros((2, 2)), np.ones((2, K)), 0.0)
         assert ei.value.code == mm.MMVM_E_UNSUPPORTED
+
+
+def test_far_field_matches_full_jet(mm):
+    """Mixed precision with and without the far-field (point-vortex) tiles."""
+    wl = mmvm_inputs.two_patches(n=4096, order=6, sigma=0.1)
+    rng = np.random.default_rng(3)
+    wl.moments[:, 3:] = rng.normal(size=wl.moments[:, 3:].shape) * 1e-3 * wl.moments[:, :1] \
+        * wl.lam0 ** 2
+    res = {}
+    for name, flags in (("far", 0), ("full", mm.MMVM_FLAG_NO_FAR_FIELD)):
+        with mm.Context(6, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32, flags=flags) as ctx:
+            ctx.set_state(wl.x, wl.moments, 0.0)
+            res[name] = ctx.rhs()
+    assert vel_error(res["far"][0], res["full"][0]) <= 1e-6
+    assert rhs_error(res["far"][1], res["full"][1], 6, wl.lam0) <= 1e-6
+    rows = np.random.default_rng(4).choice(wl.n, 6, replace=False)
+    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, 6, wl.lam0, wl.nu, rows=rows)
+    assert vel_error(res["far"][0][rows], ox) <= MIXED_RHS_TOL
+    assert rhs_error(res["far"][1][rows], oM, 6, wl.lam0) <= MIXED_RHS_TOL
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_every_kernel_variant(mm, order, monkeypatch):
+    """Each compiled all-pairs variant reproduces the oracle (mixed precision)."""
+    wl = mmvm_inputs.random_disk(n=300, order=order, radius=3.0, sigma=0.45, amp=0.02,
+                                 seed=40 + order)
+    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu)
+    seen = set()
+    for v in range(4):
+        monkeypatch.setenv("MMVM_PAIR_VARIANT", str(v))
+        ctx = mm.Context(order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32)
+        try:
+            ctx.set_state(wl.x, wl.moments, 0.0)
+        except mm.MMVMError as err:
+            ctx.close()
+            assert err.code == mm.MMVM_E_INVALID_ARG  # no such variant
+            break
+        cfg = mm.mmvm_pair_config(ctx.handle)
+        gx, gM = ctx.rhs()
+        ctx.close()
+        assert cfg["variant"] == v
+        seen.add(v)
+        assert vel_error(gx, ox) <= MIXED_RHS_TOL, cfg
+        assert rhs_error(gM, oM, order, wl.lam0) <= MIXED_RHS_TOL, cfg
+    assert len(seen) >= 3
