@@ -159,6 +159,35 @@ int mmvm_pair_config(const mmvm_ctx* ctx, int32_t* out);
  * counted.  Waits for the context stream.                                   */
 int mmvm_pair_counts(mmvm_ctx* ctx, int64_t* near_pairs, int64_t* far_pairs);
 
+/* Right-hand side without any device allocation.  The paper has no
+ * counterpart: this is a variant of mmvm_rhs_device for callers that cannot
+ * call cudaMalloc (an application that owns all device memory through its own
+ * pool or budget, a latency-critical path on which cudaMalloc/cudaFree would
+ * synchronise the device, a plugin whose host forbids allocation at run time).
+ *
+ * Computes dx/dt and dM/dt of the state (d_x: n x 2, d_moments: n x K, both
+ * device memory, row-major FP64, column order as mmvm_set_state) at time t,
+ * with the order, precision, lambda0 and nu of *cfg (cfg->device and
+ * cfg->flags are ignored: the current device is used and the far field is
+ * off), into the caller's device buffers d_dxdt (n x 2) and d_dMdt (n x K).
+ * stream: a cudaStream_t (NULL: the legacy default stream); the call is
+ * asynchronous on it, except that the first call on a device, and the first
+ * call after a change of order, upload the coefficient tables and wait for
+ * them (that call also waits for the whole device when it replaces the tables
+ * of another order); make such calls before any stream capture.
+ *
+ * All scratch lives in one fixed array of 12 MiB (12,583,168 bytes) of
+ * device memory per GPU that loads the library, held until the process exits.  Limits: 1 <= n <=
+ * 4096 and order <= 8, else MMVM_E_UNSUPPORTED with a message; nothing is
+ * allocated (no cudaMalloc, cudaFree or allocating library call).  Every call
+ * shares that array, so calls whose work overlaps on the GPU (different
+ * streams or host threads) race; serialise them.  Errors: MMVM_E_INVALID_ARG
+ * (null pointer, bad precision, lambda0 <= 0, nu < 0, non-finite t),
+ * MMVM_E_DEVICE (CUDA error).  Inputs are not scanned for non-finite values
+ * or zero circulation.                                                      */
+int mmvm_rhs_noalloc(const mmvm_config* cfg, int64_t n, double t, const double* d_x,
+                     const double* d_moments, double* d_dxdt, double* d_dMdt, void* stream);
+
 /* Measured fused-multiply-add peak of a device, in flop/s (2 flops per FMA):
  * a full-occupancy grid of independent FMA chains, about 50 ms, timed with
  * CUDA events on a stream of its own.  precision selects the FP64 or the

@@ -53,6 +53,7 @@ EXPORTS = (
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
     "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_enable_timing",
     "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_counts", "mmvm_alu_peak",
+    "mmvm_rhs_noalloc",
 )
 
 
@@ -114,6 +115,9 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_enable_timing.restype = ctypes.c_int
     lib.mmvm_pair_time.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
     lib.mmvm_pair_time.restype = ctypes.c_int
+    lib.mmvm_rhs_noalloc.argtypes = [ctypes.POINTER(mmvm_config), ctypes.c_int64, ctypes.c_double,
+                                     P, P, P, P, P]
+    lib.mmvm_rhs_noalloc.restype = ctypes.c_int
     lib.mmvm_alu_peak.argtypes = [ctypes.c_int32, ctypes.c_int32,
                                   ctypes.POINTER(ctypes.c_double)]
     lib.mmvm_alu_peak.restype = ctypes.c_int
@@ -221,6 +225,17 @@ def mmvm_pair_time(h):
     cnt = ctypes.c_int64()
     _check(load_library().mmvm_pair_time(h, ctypes.byref(ms), ctypes.byref(cnt)))
     return ms.value, cnt.value
+
+
+def mmvm_rhs_noalloc(order: int, lambda0: float, nu: float, precision: int, n: int, t: float,
+                     d_x: int, d_moments: int, d_dxdt: int, d_dMdt: int,
+                     stream: int = 0) -> None:
+    """Right-hand side from caller-owned device buffers, with no allocation
+    (fixed scratch: n <= 4096, order <= 8); runs on the current device."""
+    cfg = mmvm_config(order, precision, lambda0, nu, 0, 0)
+    _check(load_library().mmvm_rhs_noalloc(
+        ctypes.byref(cfg), int(n), float(t), ctypes.c_void_p(d_x), ctypes.c_void_p(d_moments),
+        ctypes.c_void_p(d_dxdt), ctypes.c_void_p(d_dMdt), ctypes.c_void_p(stream)))
 
 
 def mmvm_alu_peak(device: int = 0, precision: int = MMVM_MIXED_FP32) -> float:
