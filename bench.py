@@ -25,6 +25,16 @@ roofline   the all-pairs kernel (~99% of the step) against the FP32 FMA peak
            far_flops_per_pair).
 fp64       the plain FP64 form of the same right-hand side on the first 16384
            particles of the workload (one right-hand side, device-timed).
+served     the served stream (independent random-disk solves: n log-uniform in
+           [64, 8192], M in {2, 4, 8}, Re uniform in [100, 5000], 50-500 RK4
+           steps of 0.01) through the continuous-batching server: a burst
+           (every request at t = 0) gives the saturation throughput, then
+           Poisson arrivals at 0.7x the saturation request rate give p50/p99
+           latency (submit -> result on the host; a request whose state leaves
+           the finite range stops there with MMVM_E_NUMERIC and is counted
+           apart); the smallest requests are
+           re-run in the plain FP64 form (context API) for their error, and
+           a few in FP64 through the server for the mixed/FP64 ratio.
 cpu_baseline / --impl reference: the FP64 numpy oracle on sampled target rows
            against all sources, on the host cores.
 N > 1 GPUs (torchrun): independent replicas of the workload, one per GPU.
@@ -207,6 +217,141 @@ def run_reference(args, wl):
 
 
 # ---------------------------------------------------------------- ours
+def _served_requests(count):
+    return mmvm_inputs.served_stream(count=count, rate=1.0)
+
+
+def _wait_all(srv, tickets):
+    out = {}
+    pending = set(tickets)
+    while pending:
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                out[t] = r
+                pending.discard(t)
+        time.sleep(0.0005)
+    return out
+
+
+def _ok(r):
+    return r is not None and not isinstance(r[0], str)
+
+
+def _run_stream(mm, reqs, precision, arrivals=None):
+    """Submit reqs (at their arrival times, seconds from start, or all at once)
+    and collect (result or error, latency_ms) per request; returns results and
+    the makespan in seconds."""
+    results = [None] * len(reqs)
+    with mm.Server(precision=precision) as srv:
+        t0 = time.perf_counter()
+        tickets = {}
+        order = sorted(range(len(reqs)), key=lambda i: arrivals[i] if arrivals else 0.0)
+        nxt = 0
+        while nxt < len(order) or tickets:
+            now = time.perf_counter() - t0
+            while nxt < len(order) and (arrivals is None or arrivals[order[nxt]] <= now):
+                i = order[nxt]
+                w = reqs[i].workload
+                tickets[srv.submit(w.x, w.moments, w.order, w.lam0, w.nu, w.dt, w.steps)] = i
+                nxt += 1
+            for t in list(tickets):
+                try:
+                    r = srv.poll(t)
+                except mm.MMVMError as e:
+                    results[tickets.pop(t)] = ("error", str(e), getattr(e, "info", {}))
+                    continue
+                if r is not None:
+                    results[tickets.pop(t)] = r
+            time.sleep(0.0005)
+        makespan = time.perf_counter() - t0
+        stats = srv.stats()
+    return results, makespan, stats
+
+
+def run_served(args, mm):
+    """Served-stream measurement (see the module docstring)."""
+    reqs = _served_requests(args.serve_requests)
+    work = [4 * r.workload.n ** 2 * r.workload.steps for r in reqs]
+    mixed = mm.MMVM_MIXED_FP32
+    burst, span_b, st_b = _run_stream(mm, reqs, mixed)
+    ok_b = [i for i, r in enumerate(burst) if _ok(r)]
+
+    def done_work(res):  # pair interactions computed (a diverged request stops early)
+        tot = 0
+        for i, r in enumerate(res):
+            if r is not None:
+                steps = r[2].get("steps", 0) if isinstance(r[2], dict) else 0
+                tot += 4 * reqs[i].workload.n ** 2 * steps
+        return tot
+
+    sat_rate = len(reqs) / span_b
+    lam = 0.7 * sat_rate
+    arrivals = [r.arrival / lam for r in reqs]  # the stream's own exponential gaps, rescaled
+    pois, span_p, st_p = _run_stream(mm, reqs, mixed, arrivals)
+    ok_p = [i for i, r in enumerate(pois) if _ok(r)]
+    lat = np.array([pois[i][2]["latency_ms"] for i in ok_p])
+    qms = np.array([pois[i][2]["queue_ms"] for i in ok_p])
+    diverged = [i for i, r in enumerate(pois) if r is not None and not _ok(r)
+                and "NUMERIC" in r[1]]
+    lat_div = np.array([pois[i][2].get("latency_ms", np.nan) for i in diverged])
+    # errors of the served mixed results against the plain FP64 form (context API)
+    from tests.parity_util import state_error
+
+    small = sorted(ok_b, key=lambda i: work[i])[:args.serve_check]
+    errs = []
+    for i in small:
+        w = reqs[i].workload
+        with mm.Context(w.order, w.lam0, w.nu, mm.MMVM_FP64,
+                        flags=mm.MMVM_FLAG_NO_FAR_FIELD) as c64:
+            c64.set_state(w.x, w.moments, 0.0)
+            c64.step(w.dt, w.steps)
+            x64, m64, t64 = c64.get_state()
+        lam_t = math.sqrt(w.lam0 ** 2 + 4 * w.nu * t64)
+        x, m, _ = burst[i]
+        errs.append({"n": w.n, "order": w.order, "steps": w.steps,
+                     "x_rel_lambda": float(np.abs(x - x64).max() / lam_t),
+                     "M_rel_weighted": state_error(m, m64, w.order, lam_t)})
+    # the same few requests in FP64 through the server, against mixed
+    sub = sorted(ok_b, key=lambda i: work[i])[:args.serve_fp64]
+    r64, span64, _ = _run_stream(mm, [reqs[i] for i in sub], mm.MMVM_FP64)
+    r32, span32, _ = _run_stream(mm, [reqs[i] for i in sub], mixed)
+    sub_work = sum(work[i] for i in sub)
+    return {
+        "workload": f"{len(reqs)} random-disk solves: n log-uniform [64, 8192], M in {{2,4,8}}, "
+                    "Re U[100,5000], 50-500 RK4 steps of 0.01 (moments 1% per moment in the "
+                    "weighted norm), mixed precision, far field off",
+        "requests": len(reqs),
+        "pair_interactions": float(sum(work)),
+        "pair_interactions_done": float(done_work(burst)),
+        "saturation": {"makespan_s": span_b, "value": done_work(burst) / span_b,
+                       "unit": UNIT, "requests_per_s": sat_rate,
+                       "completed": len(ok_b), "max_batch": st_b["max_batch"],
+                       "ticks": st_b["ticks"]},
+        "poisson": {"rate_per_s": lam, "makespan_s": span_p,
+                    "value": done_work(pois) / span_p, "unit": UNIT,
+                    "completed": len(ok_p),
+                    "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                    "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                    "mean_ms": float(lat.mean()) if len(lat) else None,
+                    "queue_p50_ms": float(np.percentile(qms, 50)) if len(qms) else None,
+                    "max_batch": st_p["max_batch"],
+                    "diverged": len(diverged),
+                    "diverged_p50_ms": float(np.median(lat_div)) if len(lat_div) else None},
+        "not_finite": [{"request": i, "n": reqs[i].workload.n, "order": reqs[i].workload.order,
+                        "steps_done": burst[i][2].get("steps") if burst[i] else None,
+                        "steps": reqs[i].workload.steps}
+                       for i in range(len(reqs)) if i not in ok_b],
+        "note": "requests whose state leaves the finite range (the truncated moment ODE of "
+                "dense mixed-sign random disks at M >= 4) stop at that step with "
+                "MMVM_E_NUMERIC; p50/p99 are over the requests that finished",
+        "error_vs_fp64": errs,
+        "fp64_same_requests": {"requests": len(sub), "pair_interactions": float(sub_work),
+                               "fp64_value": sub_work / span64, "mixed_value": sub_work / span32,
+                               "mixed_over_fp64": span64 / span32},
+    }
+
+
 def run_ours(args, wl, rank, world, local_rank):
     import torch
 
@@ -361,6 +506,8 @@ def run_ours(args, wl, rank, world, local_rank):
                                           "flop x 2.07 GHz = %.1f TFLOP/s" % FP32_PEAK_TFLOPS,
                              "frac_of_nominal": achieved / FP32_PEAK_TFLOPS},
                 "fp64": fp64}
+        if args.serve_requests > 0:
+            line["served"] = run_served(args, mm)
         if not args.skip_cpu:
             rate, secs, sel, ox, oM = oracle_rate(wl, args.oracle_rows)
             line["cpu_baseline"] = {
@@ -388,6 +535,12 @@ def main():
     ap.add_argument("--oracle-rows", type=int, default=2)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the served stream (0: skip the serving measurement)")
+    ap.add_argument("--serve-check", type=int, default=3,
+                    help="smallest served requests re-run in FP64 for their error")
+    ap.add_argument("--serve-fp64", type=int, default=4,
+                    help="smallest served requests run through an FP64 server as well")
     ap.add_argument("--n", type=int, default=65536,
                     help="particles (the benchmark is 65536; smaller only for profiling)")
     args = ap.parse_args()

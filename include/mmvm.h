@@ -195,6 +195,95 @@ int mmvm_rhs_noalloc(const mmvm_config* cfg, int64_t n, double t, const double* 
  * of the method.  Returns MMVM_E_DEVICE on a CUDA error.                     */
 int mmvm_alu_peak(int32_t device, int32_t precision, double* flops_per_s);
 
+/* ------------------------------------------------------------------------
+ * Serving: many independent simulations (different n, order, lambda0, nu,
+ * dt, step counts) on one GPU at once, with continuous batching.
+ *
+ * A server owns one worker thread.  Submitted requests wait in a FIFO queue
+ * and are admitted between RK4 steps while their device footprint
+ * (mmvm_request_footprint) fits the HBM budget; admitted simulations keep
+ * their state on the device and advance one RK4 step per tick together (one
+ * graph-captured tick: per order, a persistent all-pairs launch over every
+ * admitted simulation of that order); a simulation leaves the batch at the
+ * end of the tick in which it completes nsteps.  The result of a request
+ * does not depend on the other requests in the batch (the split of its pairs
+ * into work items depends on its own size only).  The far field is not used
+ * (every pair takes the full jet).  Submit, poll and stats are thread-safe.
+ * ---------------------------------------------------------------------- */
+typedef struct mmvm_server mmvm_server;
+
+typedef struct {
+  int32_t device;            /* CUDA device ordinal                          */
+  int32_t precision;         /* MMVM_FP64 or MMVM_MIXED_FP32, every request  */
+  uint64_t hbm_budget_bytes; /* admission budget; 0: half the free device
+                                memory at creation                          */
+  int32_t max_active;        /* most simulations in one tick; 0: 256         */
+  uint32_t flags;            /* reserved, must be 0                          */
+} mmvm_server_config;
+
+/* One simulation: the state of eq:vorticity_decomposition at t0 (layouts as
+ * mmvm_set_state: x n x 2, moments n x K with K = (order+1)(order+2)/2; both
+ * copied by mmvm_submit), the core lambda(t)^2 = lambda0^2 + 4 nu t, and
+ * nsteps classic RK4 steps of size dt.                                      */
+typedef struct {
+  int32_t order;
+  double lambda0;
+  double nu;
+  double t0;
+  double dt;
+  int64_t nsteps;
+  int64_t n;
+  const double* x;
+  const double* moments;
+} mmvm_request;
+
+typedef struct {
+  int32_t status;     /* MMVM_OK, MMVM_PENDING or the request's error       */
+  int32_t order;
+  int64_t n;
+  int64_t steps_done;
+  double t;           /* time of the state (t0 + steps_done dt)             */
+  double queue_ms;    /* submit -> admitted (so far, while queued)          */
+  double latency_ms;  /* submit -> result ready (so far, while pending)     */
+} mmvm_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, queued, active;
+  int64_t ticks;             /* RK4 steps of the batch                       */
+  int64_t max_batch;         /* most simulations in one tick                 */
+  double pair_interactions;  /* sum over ticks of 4 sum_i n_i^2              */
+  double busy_ms;            /* host wall time of the ticks                  */
+  uint64_t footprint_bytes;  /* admitted footprint now                       */
+  uint64_t peak_footprint_bytes;
+  uint64_t budget_bytes;
+} mmvm_server_counters;
+
+/* Create a server on cfg->device (starts its worker thread).  Errors:
+ * MMVM_E_INVALID_ARG, MMVM_E_DEVICE.                                         */
+int mmvm_server_create(const mmvm_server_config* cfg, mmvm_server** out);
+/* Stop the worker (after the tick in flight), free everything; requests not
+ * yet polled are dropped.                                                   */
+void mmvm_server_destroy(mmvm_server* srv);
+/* Queue a request; *ticket identifies it for mmvm_poll.  Validates like
+ * mmvm_create + mmvm_set_state (MMVM_E_INVALID_ARG, MMVM_E_UNSUPPORTED,
+ * MMVM_E_NUMERIC, MMVM_E_ZERO_CIRCULATION) and rejects a request whose
+ * footprint exceeds the whole budget (MMVM_E_OOM).                          */
+int mmvm_submit(mmvm_server* srv, const mmvm_request* req, uint64_t* ticket);
+/* MMVM_PENDING while queued or running (res, if given, shows the progress);
+ * when done, copies the final state into x_out (n x 2) and moments_out
+ * (n x K) if they are non-null, fills res, forgets the ticket and returns
+ * MMVM_OK or the request's error (MMVM_E_NUMERIC if the state became
+ * non-finite, MMVM_E_OOM / MMVM_E_DEVICE from the device).  Unknown ticket:
+ * MMVM_E_INVALID_ARG.                                                       */
+int mmvm_poll(mmvm_server* srv, uint64_t ticket, double* x_out, double* moments_out,
+              mmvm_result* res);
+/* Counters of the server (see mmvm_server_counters).                           */
+int mmvm_server_stats(mmvm_server* srv, mmvm_server_counters* out);
+/* Device bytes a request of (order, precision, n) holds while admitted:
+ * FP64 state (6 n (2+K) doubles: step start, stage, RK4 sum), source records,
+ * partial sums, work lists.  Host-only.                                     */
+int mmvm_request_footprint(int32_t order, int32_t precision, int64_t n, uint64_t* bytes);
+
 /* Message for the calling thread's last error ("" if none).                 */
 const char* mmvm_last_error(void);
 

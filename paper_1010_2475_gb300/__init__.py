@@ -53,7 +53,8 @@ EXPORTS = (
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
     "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_enable_timing",
     "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_counts", "mmvm_alu_peak",
-    "mmvm_rhs_noalloc",
+    "mmvm_rhs_noalloc", "mmvm_server_create", "mmvm_server_destroy", "mmvm_submit",
+    "mmvm_poll", "mmvm_server_stats", "mmvm_request_footprint",
 )
 
 
@@ -67,6 +68,35 @@ class mmvm_config(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("lambda0", ctypes.c_double), ("nu", ctypes.c_double),
                 ("device", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class mmvm_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class mmvm_request(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("lambda0", ctypes.c_double),
+                ("nu", ctypes.c_double), ("t0", ctypes.c_double), ("dt", ctypes.c_double),
+                ("nsteps", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("x", ctypes.POINTER(ctypes.c_double)),
+                ("moments", ctypes.POINTER(ctypes.c_double))]
+
+
+class mmvm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("order", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("steps_done", ctypes.c_int64), ("t", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class mmvm_server_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("active", ctypes.c_int64), ("ticks", ctypes.c_int64),
+                ("max_batch", ctypes.c_int64), ("pair_interactions", ctypes.c_double),
+                ("busy_ms", ctypes.c_double), ("footprint_bytes", ctypes.c_uint64),
+                ("peak_footprint_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64)]
 
 
 _lib_handle = None
@@ -126,6 +156,19 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_pair_counts.restype = ctypes.c_int
     lib.mmvm_pair_config.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
     lib.mmvm_pair_config.restype = ctypes.c_int
+    lib.mmvm_server_create.argtypes = [ctypes.POINTER(mmvm_server_config), ctypes.POINTER(P)]
+    lib.mmvm_server_create.restype = ctypes.c_int
+    lib.mmvm_server_destroy.argtypes = [P]
+    lib.mmvm_server_destroy.restype = None
+    lib.mmvm_submit.argtypes = [P, ctypes.POINTER(mmvm_request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.mmvm_submit.restype = ctypes.c_int
+    lib.mmvm_poll.argtypes = [P, ctypes.c_uint64, D, D, ctypes.POINTER(mmvm_result)]
+    lib.mmvm_poll.restype = ctypes.c_int
+    lib.mmvm_server_stats.argtypes = [P, ctypes.POINTER(mmvm_server_counters)]
+    lib.mmvm_server_stats.restype = ctypes.c_int
+    lib.mmvm_request_footprint.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_uint64)]
+    lib.mmvm_request_footprint.restype = ctypes.c_int
     lib.mmvm_last_error.argtypes = []
     lib.mmvm_last_error.restype = ctypes.c_char_p
     _lib_handle = lib
@@ -304,3 +347,90 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ------------------------------------------------------------------ serving
+def mmvm_request_footprint(order: int, precision: int, n: int) -> int:
+    """Device bytes a request holds while admitted (host-only computation)."""
+    v = ctypes.c_uint64()
+    _check(load_library().mmvm_request_footprint(order, precision, n, ctypes.byref(v)))
+    return v.value
+
+
+class Server:
+    """Continuous-batching request loop (mmvm_server_*): submit simulations,
+    poll for their final states."""
+
+    def __init__(self, precision: int = MMVM_MIXED_FP32, device: int = 0,
+                 hbm_budget_bytes: int = 0, max_active: int = 0):
+        self.handle = ctypes.c_void_p()
+        cfg = mmvm_server_config(device, precision, hbm_budget_bytes, max_active, 0)
+        _check(load_library().mmvm_server_create(ctypes.byref(cfg), ctypes.byref(self.handle)))
+        self._orders = {}
+
+    def submit(self, x, moments, order: int, lambda0: float, nu: float, dt: float,
+               nsteps: int, t0: float = 0.0) -> int:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        moments = np.ascontiguousarray(moments, dtype=np.float64)
+        n = x.shape[0]
+        if x.shape != (n, 2) or moments.shape != (n, (order + 1) * (order + 2) // 2):
+            raise ValueError("x must be (n, 2) and moments (n, K)")
+        req = mmvm_request(order, lambda0, nu, t0, dt, nsteps, n, _dptr(x), _dptr(moments))
+        ticket = ctypes.c_uint64()
+        _check(load_library().mmvm_submit(self.handle, ctypes.byref(req), ctypes.byref(ticket)))
+        self._orders[ticket.value] = (order, n)
+        return ticket.value
+
+    def poll(self, ticket: int):
+        """None while pending; else (x, moments, info dict)."""
+        order, n = self._orders[ticket]
+        K = (order + 1) * (order + 2) // 2
+        x = np.empty((n, 2))
+        m = np.empty((n, K))
+        res = mmvm_result()
+        rc = load_library().mmvm_poll(self.handle, ticket, _dptr(x), _dptr(m), ctypes.byref(res))
+        if rc == MMVM_PENDING:
+            return None
+        del self._orders[ticket]
+        info = {"t": res.t, "steps": res.steps_done, "queue_ms": res.queue_ms,
+                "latency_ms": res.latency_ms}
+        try:
+            _check(rc)
+        except MMVMError as e:  # the request failed; its timing is still known
+            e.info = info
+            raise
+        return x, m, info
+
+    def wait(self, ticket: int, timeout: float = 600.0, interval: float = 0.0005):
+        import time
+
+        t_end = time.monotonic() + timeout
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.monotonic() > t_end:
+                raise TimeoutError(f"request {ticket} still pending after {timeout} s")
+            time.sleep(interval)
+
+    def stats(self) -> dict:
+        st = mmvm_server_counters()
+        _check(load_library().mmvm_server_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in mmvm_server_counters._fields_}
+
+    def close(self):
+        if self.handle:
+            load_library().mmvm_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

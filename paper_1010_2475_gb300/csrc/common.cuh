@@ -61,6 +61,29 @@ __host__ __device__ constexpr int rec_len(int M) {
 // unit of the bounding boxes used for the far-field test.
 constexpr int kGroup = 32;
 
+// One instance (an independent simulation) of a batch of one order.
+//  * state: FP64 blocks y_x (n x 2), y_M (n x K), ys_x, ys_M (RK4 stage
+//    state), sum_x, sum_M (RK4 running sum), one after another;
+//  * records: n, starting at record slot0 of the batch (slot0 is a multiple
+//    of kGroup, so every group of kGroup slots belongs to one instance);
+//  * sources split into `chunks` chunks of chunk_len (a multiple of kGroup);
+//    partial sums [chunk][beta][target] start part_off doubles into the
+//    batch's partials;
+//  * core lambda^2 = lam0sq + four_nu t; step size dt; t is advanced on the
+//    device after every step.
+struct BatchInst {
+  double* state;
+  int n;
+  int slot0;
+  int chunk_len;
+  int chunks;
+  long long part_off;
+  double lam0sq;
+  double four_nu;
+  double t;
+  double dt;
+};
+
 // Far-field threshold on x = |b|^2 (c = 1 units) per order M: beyond it the
 // Gaussian part of every jet entry of order <= 3M is below 2^-25 of the
 // largest entry of that order (measured against the FP64 oracle's jet over

@@ -24,11 +24,26 @@ constexpr int kMINB = kSpec.MINB;
 constexpr bool kSYNC = kSpec.SYNC != 0;
 static_assert(kTPC % 32 == 0, "targets per CTA must be whole warps");
 #define MMVM_KERNEL pair_kernel<kM, T, kLO, kHI, kTPC, kMINB, kSYNC>
+#define MMVM_BATCH_KERNEL pair_batch_kernel<kM, T, kLO, kHI, kTPC, kMINB, kSYNC>
 
 size_t smem_fn(int S) { return pair_smem_bytes<kM, T, kLO, kHI, kTPC>(S); }
 cudaError_t prepare_fn(int S) {
-  return cudaFuncSetAttribute(MMVM_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(MMVM_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_fn(S));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(MMVM_BATCH_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_fn(S));
+}
+cudaError_t launch_batch_fn(const void* rec, const BatchInst* inst, const int4* items,
+                            const int* n_items, int* counter, int grid, int S, double* partial,
+                            cudaStream_t st) {
+  MMVM_BATCH_KERNEL<<<grid, kTPC, smem_fn(S), st>>>(static_cast<const T*>(rec), inst, items,
+                                                    n_items, counter, S, partial);
+  return cudaGetLastError();
+}
+cudaError_t occ_batch_fn(int S, int* blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, MMVM_BATCH_KERNEL, kTPC,
+                                                       smem_fn(S));
 }
 cudaError_t launch_fn(const void* rec, int n, int chunk_len, int gy, int S, const void* gbox,
                       double* partial, unsigned long long* counts, cudaStream_t st) {
@@ -54,6 +69,8 @@ SliceEntry MMVM_SLICE(MMVM_INST_M, MMVM_INST_PREC, MMVM_INST_V, MMVM_INST_S)() {
   e.prepare = prepare_fn;
   e.launch = launch_fn;
   e.occupancy = occ_fn;
+  e.launch_batch = launch_batch_fn;
+  e.occupancy_batch = occ_batch_fn;
   return e;
 }
 

@@ -104,31 +104,33 @@ __device__ __forceinline__ bool tile_is_far(const float4* __restrict__ gbox, int
   return dx * dx + dy * dy >= x_far(M);
 }
 
-// gbox: per group of kGroup consecutive records, (min z1, max z1, min z2,
-// max z2) of the hi parts; null disables the far-field path (FP64 always).
-// Layout of `partial`: [chunk][beta column][target] FP64 (coalesced writes);
-// this kernel writes the columns of its slice only.  counts (nullable):
-// cumulative (near, far) pair counts, added by the first slice only.
-template <int M, typename T, int LO, int HI, int TPC, int MINB, bool SYNC>
-__global__ void __launch_bounds__(TPC, MINB)
-    pair_kernel(const T* __restrict__ rec, int n, int chunk_len, int S,
-                const float4* __restrict__ gbox, double* __restrict__ partial,
-                unsigned long long* __restrict__ counts) {
+// The work of one CTA: targets tile0 .. tile0 + TPC - 1 (those below n) of
+// one instance against its sources c0 .. c1 - 1.  rec holds the instance's n
+// records (indices are local to it); gbox: per group of kGroup consecutive
+// records, (min z1, max z1, min z2, max z2) of the hi parts, null disables the
+// far-field path (FP64 always).  out: this chunk's block [NB][n] of the
+// partial sums (coalesced FP64 stores); only the slice's columns are written.
+// counts (nullable): cumulative (near, far) pair counts, added by the first
+// slice only.  Called by every thread of the CTA; begins by writing only its
+// own shared-memory slots and reuses the tile only after a barrier, so a
+// persistent CTA may call it for one item after another.
+template <int M, typename T, int LO, int HI, int TPC, bool SYNC>
+__device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n, int tile0, int c0,
+                                               int c1, int S, const float4* __restrict__ gbox,
+                                               double* __restrict__ out,
+                                               unsigned long long* __restrict__ counts,
+                                               unsigned char* smem_raw) {
   using PN = PairNear<M, T, LO, HI>;
   constexpr int R = rec_len<T>(M);
-  constexpr int NB = n_beta(M);
   constexpr int NBL = PN::NBL;
   constexpr int NY = HI - LO + 1;
   constexpr bool f32 = std::is_same<T, float>::value;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
   float* acc_hi = reinterpret_cast<float*>(tile + (size_t)S * R);
   float* acc_lo = acc_hi + NBL * TPC;
   const int warp = threadIdx.x >> 5;
   const int slot = threadIdx.x;
-  const int j = blockIdx.x * TPC + slot;
-  const int c0 = blockIdx.y * chunk_len;
-  const int c1 = min(n, c0 + chunk_len);
+  const int j = tile0 + slot;
   T tz1, tz2, tl1 = T(0), tl2 = T(0);
   if (j < n) {
     const T* r = rec + (size_t)j * R;
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(TPC, MINB)
   unsigned n_near = 0, n_far = 0;  // pairs of this thread's target on each path
   // this warp's 32 targets form one group; a warp wholly past n does no work
   // (but still takes part in every barrier)
-  const int wfirst = blockIdx.x * TPC + warp * 32;
+  const int wfirst = tile0 + warp * 32;
   const bool warp_valid = wfirst < n;
   const int tgroup = wfirst / kGroup;
   auto load_tile = [&](int t0, int cnt) {
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(TPC, MINB)
     }
   }
   if (j < n) {
-    double* out = partial + (size_t)blockIdx.y * NB * n + (size_t)PN::B0 * n + j;
+    double* o = out + (size_t)PN::B0 * n + j;
 #pragma unroll
     for (int b = 0; b < NBL; ++b) {
       double v;
@@ -238,8 +240,56 @@ __global__ void __launch_bounds__(TPC, MINB)
       } else {
         v = acc[b];
       }
-      out[(size_t)b * n] = v;
+      o[(size_t)b * n] = v;
     }
+  }
+}
+
+// One context: grid (target tiles, source chunks) over n records.
+// Layout of `partial`: [chunk][beta column][target] FP64.
+template <int M, typename T, int LO, int HI, int TPC, int MINB, bool SYNC>
+__global__ void __launch_bounds__(TPC, MINB)
+    pair_kernel(const T* __restrict__ rec, int n, int chunk_len, int S,
+                const float4* __restrict__ gbox, double* __restrict__ partial,
+                unsigned long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NB = n_beta(M);
+  const int c0 = blockIdx.y * chunk_len;
+  const int c1 = min(n, c0 + chunk_len);
+  pair_tile_work<M, T, LO, HI, TPC, SYNC>(rec, n, blockIdx.x * TPC, c0, c1, S, gbox,
+                                          partial + (size_t)blockIdx.y * NB * n, counts,
+                                          smem_raw);
+}
+
+// Many independent instances of one order in one persistent launch: every
+// CTA takes work items (instance, target tile, source chunk) from a shared
+// counter until none is left.  Items are listed by the host, costliest first.
+// The counter must be zero at launch (the caller clears it).
+template <int M, typename T, int LO, int HI, int TPC, int MINB, bool SYNC>
+__global__ void __launch_bounds__(TPC, MINB)
+    pair_batch_kernel(const T* __restrict__ rec, const BatchInst* __restrict__ inst,
+                      const int4* __restrict__ items, const int* __restrict__ n_items,
+                      int* __restrict__ counter, int S, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int item_s;
+  constexpr int NB = n_beta(M);
+  constexpr int R = rec_len<T>(M);
+  const int total = *n_items;
+#pragma unroll 1
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = item_s;
+    __syncthreads();  // every thread has read item_s before it is overwritten
+    if (it >= total) break;
+    const int4 w = items[it];  // (instance, first target, chunk, -)
+    const BatchInst ip = inst[w.x];
+    const int c0 = w.z * ip.chunk_len;
+    const int c1 = min(ip.n, c0 + ip.chunk_len);
+    pair_tile_work<M, T, LO, HI, TPC, SYNC>(rec + (size_t)ip.slot0 * R, ip.n, w.y, c0, c1, S,
+                                            nullptr,
+                                            partial + ip.part_off + (size_t)w.z * NB * ip.n,
+                                            nullptr, smem_raw);
   }
 }
 

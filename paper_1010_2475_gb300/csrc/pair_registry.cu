@@ -149,4 +149,28 @@ cudaError_t pair_launch(const PairEntry& e, const void* rec, int n, int chunks, 
   return cudaSuccess;
 }
 
+int pair_batch_occupancy(const PairEntry& e, int S) {
+  int best = 1 << 30;
+  for (int s = 0; s < e.nslices; ++s) {
+    int b = 0;
+    if (e.slices[s].occupancy_batch(S, &b) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    best = std::min(best, b);
+  }
+  return e.nslices ? best : 0;
+}
+
+cudaError_t pair_launch_batch(const PairEntry& e, const void* rec, const BatchInst* inst,
+                              const int4* items, const int* n_items, int* counters, int grid,
+                              int S, double* partial, cudaStream_t st) {
+  for (int s = 0; s < e.nslices; ++s) {
+    cudaError_t r = e.slices[s].launch_batch(rec, inst, items, n_items, counters + s, grid, S,
+                                             partial, st);
+    if (r != cudaSuccess) return r;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace mmvm

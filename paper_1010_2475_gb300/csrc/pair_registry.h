@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "common.cuh"
 #include "pair_variants.h"
 
 namespace mmvm {
@@ -16,6 +17,11 @@ struct SliceEntry {
   cudaError_t (*launch)(const void* rec, int n, int chunk_len, int gy, int S, const void* gbox,
                         double* partial, unsigned long long* counts, cudaStream_t st) = nullptr;
   cudaError_t (*occupancy)(int S, int* blocks_per_sm) = nullptr;
+  // persistent batched form (pair_batch_kernel): `grid` CTAs
+  cudaError_t (*launch_batch)(const void* rec, const BatchInst* inst, const int4* items,
+                              const int* n_items, int* counter, int grid, int S,
+                              double* partial, cudaStream_t st) = nullptr;
+  cudaError_t (*occupancy_batch)(int S, int* blocks_per_sm) = nullptr;
 };
 
 struct PairEntry {
@@ -48,5 +54,12 @@ int pair_occupancy(const PairEntry& e, int S);
 cudaError_t pair_launch(const PairEntry& e, const void* rec, int n, int chunks, int S,
                         const void* gbox, double* partial, int grid_y_limit, cudaStream_t st,
                         unsigned long long* counts = nullptr);
+// CTAs per SM of the batched slice kernels (the smallest), 0 on error.
+int pair_batch_occupancy(const PairEntry& e, int S);
+// Launch every slice of the batched form, `grid` persistent CTAs each;
+// counters[s] (zero at launch) hands out the items to slice s.
+cudaError_t pair_launch_batch(const PairEntry& e, const void* rec, const BatchInst* inst,
+                              const int4* items, const int* n_items, int* counters, int grid,
+                              int S, double* partial, cudaStream_t st);
 
 }  // namespace mmvm

@@ -11,6 +11,8 @@
 //  * advance_time: t += dt after the fourth stage.
 #include "particle_kernels.h"
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace mmvm {
@@ -21,10 +23,54 @@ __device__ __forceinline__ double stage_c(const double* t_dev, const double* dt_
   return 2.0 * (lam0sq + four_nu * t);
 }
 
-// Sorted position p holds particle perm[p] (perm == null: identity).  FP32
-// records also get the far-field multipoles A'_n = sum_{|m|=n} a_m (-i)^{m1+n}
-// and every warp (kGroup consecutive positions) writes the bounding box of its
-// hi-part centres to gbox (if given).
+// The source record of one particle (centre xj, moments mj): zeta = x / sqrt(c)
+// (FP32: exact (hi, lo) pair), a_m = M_m c^{-|m|/2} and, for FP32 records,
+// the far-field multipoles A'_n = sum_{|m|=n} a_m (-i)^{m1+n}.
+template <typename T>
+__device__ __forceinline__ void make_record(T* __restrict__ r, const double* __restrict__ xj,
+                                            const double* __restrict__ mj, int M, int K, int R,
+                                            double irc) {
+  const double z1 = xj[0] * irc;
+  const double z2 = xj[1] * irc;
+  int h;
+  if constexpr (sizeof(T) == 4) {
+    const float h1 = (float)z1, h2 = (float)z2;
+    r[0] = h1;
+    r[1] = h2;
+    r[2] = (float)(z1 - (double)h1);
+    r[3] = (float)(z2 - (double)h2);
+    h = 4;
+  } else {
+    r[0] = (T)z1;
+    r[1] = (T)z2;
+    h = 2;
+  }
+  double sc = 1.0;
+  int col = 0;
+  for (int s = 0; s <= M; ++s) {
+    double fr = 0.0, fi = 0.0;  // A'_s
+    for (int k2 = 0; k2 <= s; ++k2, ++col) {
+      const double a = mj[col] * sc;
+      r[h + col] = (T)a;
+      switch ((s - k2 + s) & 3) {  // (-i)^{m1 + s}, m1 = s - k2
+        case 0: fr += a; break;
+        case 1: fi -= a; break;
+        case 2: fr -= a; break;
+        default: fi += a; break;
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+      r[h + K + 2 * s] = (T)fr;
+      r[h + K + 2 * s + 1] = (T)fi;
+    }
+    sc *= irc;
+  }
+  for (int q = h + K + rec_far<T>(M); q < R; ++q) r[q] = T(0);
+}
+
+// Sorted position p holds particle perm[p] (perm == null: identity).  Every
+// warp (kGroup consecutive positions) writes the bounding box of its hi-part
+// centres to gbox (if given).
 template <typename T>
 __global__ void prep_kernel(int n, int M, int K, int R, const int* __restrict__ perm,
                             const double* __restrict__ x, const double* __restrict__ mom,
@@ -36,47 +82,12 @@ __global__ void prep_kernel(int n, int M, int K, int R, const int* __restrict__ 
   if (valid) {
     const int j = perm ? perm[p] : p;
     const double c = stage_c(t_dev, dt_dev, cs, lam0sq, four_nu);
-    const double irc = 1.0 / sqrt(c);
     T* r = rec + (size_t)p * R;
-    const double z1 = x[2 * j] * irc;
-    const double z2 = x[2 * j + 1] * irc;
-    int h;
+    make_record<T>(r, x + 2 * j, mom + (size_t)j * K, M, K, R, 1.0 / sqrt(c));
     if constexpr (sizeof(T) == 4) {
-      const float h1 = (float)z1, h2 = (float)z2;
-      r[0] = h1;
-      r[1] = h2;
-      r[2] = (float)(z1 - (double)h1);
-      r[3] = (float)(z2 - (double)h2);
-      h = 4;
-      lo1 = hi1 = h1;
-      lo2 = hi2 = h2;
-    } else {
-      r[0] = (T)z1;
-      r[1] = (T)z2;
-      h = 2;
+      lo1 = hi1 = r[0];
+      lo2 = hi2 = r[1];
     }
-    const double* mj = mom + (size_t)j * K;
-    double sc = 1.0;
-    int col = 0;
-    for (int s = 0; s <= M; ++s) {
-      double fr = 0.0, fi = 0.0;  // A'_s
-      for (int k2 = 0; k2 <= s; ++k2, ++col) {
-        const double a = mj[col] * sc;
-        r[h + col] = (T)a;
-        switch ((s - k2 + s) & 3) {  // (-i)^{m1 + s}, m1 = s - k2
-          case 0: fr += a; break;
-          case 1: fi -= a; break;
-          case 2: fr -= a; break;
-          default: fi += a; break;
-        }
-      }
-      if constexpr (sizeof(T) == 4) {
-        r[h + K + 2 * s] = (T)fr;
-        r[h + K + 2 * s + 1] = (T)fi;
-      }
-      sc *= irc;
-    }
-    for (int q = h + K + rec_far<T>(M); q < R; ++q) r[q] = T(0);
   }
   if (gbox) {
 #pragma unroll
@@ -92,8 +103,10 @@ __global__ void prep_kernel(int n, int M, int K, int R, const int* __restrict__ 
 
 // Shared-memory layout per block: for each of TB targets, Psi[NB], a[K], X[2],
 // M_00 (read before any in-place stage write), then the powers c^{-s/2}.
-__global__ void finish_kernel(FinishArgs A) {
-  extern __shared__ double sm[];
+// The block handles sorted positions j0 .. j0 + TB - 1 (those below A.n); all
+// its threads call this, and it ends with the block's last writes to shared
+// memory behind no barrier (a caller that loops must add one).
+__device__ __forceinline__ void finish_block(const FinishArgs& A, int j0, double* sm) {
   const int TB = A.targets_per_block;
   const int NB = A.NB, K = A.K, M = A.M;
   double* psi = sm;                       // TB * NB
@@ -101,7 +114,6 @@ __global__ void finish_kernel(FinishArgs A) {
   double* X = at + TB * K;                // TB * 2
   double* m00s = X + TB * 2;              // TB
   double* cpow = m00s + TB;               // c^{-s/2}, s = 0..2M+2
-  const int j0 = blockIdx.x * TB;  // sorted positions; particle = perm[position]
   const double c = stage_c(A.t_dev, A.dt_dev, A.cs, A.lam0sq, A.four_nu);
   for (int s = threadIdx.x; s <= 2 * M + 2; s += blockDim.x) cpow[s] = pow(c, -0.5 * s);
   __syncthreads();
@@ -209,6 +221,11 @@ __global__ void finish_kernel(FinishArgs A) {
   }
 }
 
+__global__ void finish_kernel(FinishArgs A) {
+  extern __shared__ double sm[];
+  finish_block(A, blockIdx.x * A.targets_per_block, sm);  // sorted positions
+}
+
 __global__ void advance_time_kernel(double* t_dev, const double* dt_dev) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *t_dev += *dt_dev;
 }
@@ -223,6 +240,141 @@ __global__ void scan_state_kernel(int n, int K, const double* __restrict__ x,
   for (int m = 0; m < K; ++m) bad |= !isfinite(mom[(size_t)j * K + m]);
   if (bad) atomicOr(flags, 1);
   if (mom[(size_t)j * K] == 0.0) atomicOr(flags + 1, 1);
+}
+
+// ------------------------------------------------------------------ batches
+// Offsets of the state blocks of one instance (see BatchInst).
+__device__ __forceinline__ const double* inst_stage_x(const BatchInst& I, int K, int src) {
+  return I.state + (src ? (size_t)I.n * (2 + K) : 0);
+}
+__device__ __forceinline__ const double* inst_stage_m(const BatchInst& I, int K, int src) {
+  return inst_stage_x(I, K, src) + 2 * (size_t)I.n;
+}
+
+// Records of every instance of a batch of one order: slot p belongs to
+// instance slot_inst[p / kGroup]; padding slots past an instance's n are not
+// written (no kernel reads them).  src = 0 reads the step-start state y,
+// src = 1 the stage state ys; the core is taken at t + cs dt of each instance.
+template <typename T>
+__global__ void prep_batch_kernel(int M, int K, int R, const BatchInst* __restrict__ inst,
+                                  const int* __restrict__ slot_inst,
+                                  const int* __restrict__ n_slots, int src, double cs,
+                                  T* __restrict__ rec) {
+  const int total = *n_slots;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += gridDim.x * blockDim.x) {
+    const BatchInst& I = inst[slot_inst[p / kGroup]];
+    const int j = p - I.slot0;
+    if (j >= I.n) continue;
+    const double c = 2.0 * (I.lam0sq + I.four_nu * (I.t + cs * I.dt));
+    make_record<T>(rec + (size_t)p * R, inst_stage_x(I, K, src) + 2 * j,
+                   inst_stage_m(I, K, src) + (size_t)j * K, M, K, R, 1.0 / sqrt(c));
+  }
+}
+
+// Finish of every instance of a batch: item (instance, first target) per
+// block of TB targets; blocks loop over the items.
+__global__ void finish_batch_kernel(BatchFinishArgs B) {
+  extern __shared__ double sm[];
+  const int total = *B.n_items;
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int2 w = B.items[it];
+    const BatchInst& I = B.inst[w.x];
+    const size_t blk = (size_t)I.n * (2 + B.K);
+    FinishArgs A;
+    A.n = I.n;
+    A.M = B.M;
+    A.K = B.K;
+    A.NB = B.NB;
+    A.nchunks = I.n > 1 ? I.chunks : 0;
+    A.targets_per_block = B.targets_per_block;
+    A.partial = I.n > 1 ? B.partial + I.part_off : nullptr;
+    A.perm = nullptr;
+    A.Min = inst_stage_m(I, B.K, B.src);
+    A.k_off = B.k_off;
+    A.e_l = B.e_l;
+    A.e_b = B.e_b;
+    A.e_c = B.e_c;
+    A.psi0 = B.psi0;
+    A.lam0sq = I.lam0sq;
+    A.four_nu = I.four_nu;
+    A.t_dev = &I.t;
+    A.dt_dev = &I.dt;
+    A.cs = B.cs;
+    A.mode = B.mode;
+    A.y_x = I.state;
+    A.y_M = I.state + 2 * (size_t)I.n;
+    A.ys_x = I.state + blk;
+    A.ys_M = I.state + blk + 2 * (size_t)I.n;
+    A.sum_x = I.state + 2 * blk;
+    A.sum_M = I.state + 2 * blk + 2 * (size_t)I.n;
+    finish_block(A, w.y, sm);
+    __syncthreads();  // shared memory is reused by the next item
+  }
+}
+
+__global__ void advance_batch_kernel(BatchInst* __restrict__ inst, const int* __restrict__ n_inst) {
+  const int total = *n_inst;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+    inst[i].t += inst[i].dt;
+}
+
+// flags[i] = 1 if the step-start state of instance i holds a non-finite value,
+// else 0; one block per instance (blocks loop over the instances).
+__global__ void scan_batch_kernel(int K, const BatchInst* __restrict__ inst,
+                                  const int* __restrict__ n_inst, int* __restrict__ flags) {
+  const int total = *n_inst;
+  for (int i = blockIdx.x; i < total; i += gridDim.x) {
+    const BatchInst& I = inst[i];
+    const size_t len = (size_t)I.n * (2 + K);
+    bool bad = false;
+    for (size_t q = threadIdx.x; q < len; q += blockDim.x) bad |= !isfinite(I.state[q]);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) flags[i] = bad ? 1 : 0;
+  }
+}
+
+cudaError_t launch_scan_batch(int M, const BatchInst* inst, const int* n_inst, int max_inst,
+                              int* flags, cudaStream_t st) {
+  scan_batch_kernel<<<std::max(1, std::min(max_inst, 1024)), 256, 0, st>>>(n_moments(M), inst,
+                                                                          n_inst, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_batch(int precision, int M, const BatchInst* inst, const int* slot_inst,
+                              const int* n_slots, int max_slots, int src, double cs, void* rec,
+                              cudaStream_t st) {
+  const int K = n_moments(M);
+  const int threads = 128, blocks = std::max(1, std::min((max_slots + threads - 1) / threads, 4096));
+  if (precision == 1)
+    prep_batch_kernel<float><<<blocks, threads, 0, st>>>(M, K, rec_len<float>(M), inst, slot_inst,
+                                                         n_slots, src, cs, (float*)rec);
+  else
+    prep_batch_kernel<double><<<blocks, threads, 0, st>>>(M, K, rec_len<double>(M), inst,
+                                                          slot_inst, n_slots, src, cs,
+                                                          (double*)rec);
+  return cudaGetLastError();
+}
+
+size_t finish_smem_bytes(int M, int targets_per_block) {
+  const int K = n_moments(M), NB = n_beta(M);
+  return sizeof(double) * ((size_t)targets_per_block * (NB + K + 3) + 2 * M + 3);
+}
+
+cudaError_t launch_finish_batch(const BatchFinishArgs& B, int grid, cudaStream_t st) {
+  const size_t smem = finish_smem_bytes(B.M, B.targets_per_block);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(finish_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  finish_batch_kernel<<<std::max(1, grid), 128, smem, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_batch(BatchInst* inst, const int* n_inst, int max_inst,
+                                 cudaStream_t st) {
+  advance_batch_kernel<<<std::max(1, (max_inst + 127) / 128), 128, 0, st>>>(inst, n_inst);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prep(int precision, int n, int M, const int* perm, const double* x,

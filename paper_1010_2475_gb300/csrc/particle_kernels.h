@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace mmvm {
 
 struct FinishArgs {
@@ -31,6 +33,37 @@ struct FinishArgs {
   double* sum_x = nullptr;          // RK4 running sum
   double* sum_M = nullptr;
 };
+
+// Finish of a batch of one order (see BatchInst): items (instance, first
+// target) of targets_per_block targets each; src selects the stage input
+// (0: y, 1: ys); mode 1..4 is the RK4 stage (mode 0 is not used by batches).
+struct BatchFinishArgs {
+  int M = 0, K = 0, NB = 0;
+  int targets_per_block = 1;
+  const BatchInst* inst = nullptr;
+  const int2* items = nullptr;
+  const int* n_items = nullptr;     // device count of items
+  const double* partial = nullptr;  // the batch's partials (BatchInst::part_off)
+  const int* k_off = nullptr;       // finish tables of the order (tables.h)
+  const int* e_l = nullptr;
+  const int* e_b = nullptr;
+  const double* e_c = nullptr;
+  const double* psi0 = nullptr;
+  int src = 0;
+  double cs = 0;
+  int mode = 1;
+};
+
+cudaError_t launch_prep_batch(int precision, int M, const BatchInst* inst, const int* slot_inst,
+                              const int* n_slots, int max_slots, int src, double cs, void* rec,
+                              cudaStream_t st);
+size_t finish_smem_bytes(int M, int targets_per_block);
+// flags[i] = 1 if instance i's step-start state holds a non-finite value.
+cudaError_t launch_scan_batch(int M, const BatchInst* inst, const int* n_inst, int max_inst,
+                              int* flags, cudaStream_t st);
+cudaError_t launch_finish_batch(const BatchFinishArgs& B, int grid, cudaStream_t st);
+cudaError_t launch_advance_batch(BatchInst* inst, const int* n_inst, int max_inst,
+                                 cudaStream_t st);
 
 cudaError_t launch_prep(int precision, int n, int M, const int* perm, const double* x,
                         const double* mom, const double* t_dev, const double* dt_dev, double cs,

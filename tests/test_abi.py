@@ -68,6 +68,36 @@ def test_pure_host_entry_points(lib):
     assert lib.mmvm_create(ctypes.byref(cfg), ctypes.byref(h)) == mm.MMVM_E_INVALID_ARG
 
 
+def test_request_footprint_host_only(lib):
+    """Admission accounting of the server: FP64 state (step start, stage, RK4
+    sum), source records padded to groups of 32, one block of partial sums per
+    1024-source chunk, work lists."""
+    import paper_1010_2475_gb300 as mm
+
+    def expected(order, prec, n):
+        K = (order + 1) * (order + 2) // 2
+        NB = (2 * order + 1) * (2 * order + 2) // 2 - 1 if order > 0 else 2
+        hdr = 4 if prec == mm.MMVM_MIXED_FP32 else 2
+        eb = 4 if prec == mm.MMVM_MIXED_FP32 else 8
+        far = 2 * (order + 1) if prec == mm.MMVM_MIXED_FP32 else 0
+        align = 16 // eb
+        rec = -(-(hdr + K + far) // align) * align
+        slots = -(-n // 32) * 32
+        chunks = 0 if n <= 1 else min(-(-n // 1024), 16)
+        items = (slots // 32 + 1) * max(chunks, 1) * 16 + n * 8 + slots // 32 * 4 + 64
+        return 6 * n * (2 + K) * 8 + slots * rec * eb + chunks * NB * n * 8 + items
+
+    for order, prec, n in [(2, 1, 64), (4, 1, 4096), (8, 1, 8192), (6, 0, 1000), (10, 1, 1),
+                           (0, 0, 2)]:
+        assert mm.mmvm_request_footprint(order, prec, n) == expected(order, prec, n)
+    assert (mm.mmvm_request_footprint(8, 1, 8192) > mm.mmvm_request_footprint(4, 1, 8192)
+            > mm.mmvm_request_footprint(4, 1, 4096))
+    with pytest.raises(mm.MMVMError):
+        mm.mmvm_request_footprint(4, 1, 0)
+    with pytest.raises(mm.MMVMError):
+        mm.mmvm_request_footprint(4, 5, 10)
+
+
 def test_missing_library_fails_loudly(tmp_path):
     import paper_1010_2475_gb300 as mm
 

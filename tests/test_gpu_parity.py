@@ -62,7 +62,7 @@ def test_single_particle_rhs_fp64(mm, order):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_multi_particle_rhs(mm, order, n, prec):
     wl = mmvm_inputs.random_disk(n=n, order=order, radius=2.0 + 0.15 * n ** 0.5, sigma=0.45,
-                                 amp=0.03, seed=100 + order)
+                                 amp=0.03, moment_scale="absolute", seed=100 + order)
     t = 0.7
     ox, oM = rhs_regrouped(wl.x, wl.moments, t, order, wl.lam0, wl.nu)
     p = mm.MMVM_FP64 if prec == "fp64" else mm.MMVM_MIXED_FP32
@@ -76,7 +76,7 @@ def test_multi_particle_rhs(mm, order, n, prec):
 
 def test_literal_form_small(mm):
     """Tiny case against the literal Gamma-tensor form (no regrouping)."""
-    wl = mmvm_inputs.random_disk(n=4, order=3, radius=1.5, sigma=0.6, amp=0.05, seed=5)
+    wl = mmvm_inputs.random_disk(n=4, order=3, radius=1.5, sigma=0.6, amp=0.05, moment_scale="absolute", seed=5)
     ox, oM = rhs_literal(wl.x, wl.moments, 0.0, 3, wl.lam0, wl.nu)
     gx, gM = _gpu_rhs(mm, wl, 0.0, mm.MMVM_FP64)
     assert vel_error(gx, ox) <= FP64_TOL
@@ -103,7 +103,7 @@ def test_near_coincident_and_far_pairs(mm):
 
 
 def test_rk4_fp64_matches_oracle(mm):
-    wl = mmvm_inputs.random_disk(n=24, order=3, radius=2.0, sigma=0.5, amp=0.03, seed=3)
+    wl = mmvm_inputs.random_disk(n=24, order=3, radius=2.0, sigma=0.5, amp=0.03, moment_scale="absolute", seed=3)
     dt, nsteps = 0.02, 5
     ox, oM, ot = rk4(wl.x, wl.moments, 0.0, dt, nsteps, 3, wl.lam0, wl.nu)
     with mm.Context(3, wl.lam0, wl.nu, mm.MMVM_FP64) as ctx:
@@ -212,7 +212,7 @@ def test_far_field_matches_full_jet(mm):
 @pytest.mark.parametrize("order", [4, 6, 8])
 def test_every_kernel_variant(mm, order, monkeypatch):
     """Each compiled all-pairs variant reproduces the oracle (mixed precision)."""
-    wl = mmvm_inputs.random_disk(n=300, order=order, radius=3.0, sigma=0.45, amp=0.02,
+    wl = mmvm_inputs.random_disk(n=300, order=order, radius=3.0, sigma=0.45, amp=0.02, moment_scale="absolute",
                                  seed=40 + order)
     ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu)
     seen = set()

@@ -79,7 +79,7 @@ CASES = [
 def test_noalloc_matches_context_twice(env, order, n, prec):
     torch, mm = env
     wl = mmvm_inputs.random_disk(n=n, order=order, radius=2.0 + 0.15 * n ** 0.5, sigma=0.45,
-                                 amp=0.03, seed=700 + order)
+                                 amp=0.03, moment_scale="absolute", seed=700 + order)
     if n == 1:
         wl = mmvm_inputs.single_quadrupole(order=order, eps=0.1, sigma0=1.0)
     t = 0.4
@@ -94,8 +94,8 @@ def test_noalloc_matches_context_twice(env, order, n, prec):
 def test_noalloc_alternating_orders(env):
     """Calls that switch order re-upload the tables; results stay right."""
     torch, mm = env
-    a = mmvm_inputs.random_disk(n=300, order=3, radius=3.0, sigma=0.45, amp=0.03, seed=801)
-    b = mmvm_inputs.random_disk(n=200, order=5, radius=3.0, sigma=0.45, amp=0.03, seed=802)
+    a = mmvm_inputs.random_disk(n=300, order=3, radius=3.0, sigma=0.45, amp=0.03, moment_scale="absolute", seed=801)
+    b = mmvm_inputs.random_disk(n=200, order=5, radius=3.0, sigma=0.45, amp=0.03, moment_scale="absolute", seed=802)
     refs = {id(w): _context_rhs(mm, w, 0.2, mm.MMVM_FP64) for w in (a, b)}
     for w in (a, b, a):
         gx, gM = _noalloc_rhs(torch, mm, w, 0.2, mm.MMVM_FP64)
