@@ -320,7 +320,7 @@ def run_served(args, mm):
     return {
         "workload": f"{len(reqs)} random-disk solves: n log-uniform [64, 8192], M in {{2,4,8}}, "
                     "Re U[100,5000], 50-500 RK4 steps of 0.01 (moments 1% per moment in the "
-                    "weighted norm), mixed precision, far field off",
+                    "weighted norm), mixed precision with the far field",
         "requests": len(reqs),
         "pair_interactions": float(sum(work)),
         "pair_interactions_done": float(done_work(burst)),

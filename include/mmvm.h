@@ -200,15 +200,17 @@ int mmvm_alu_peak(int32_t device, int32_t precision, double* flops_per_s);
  * dt, step counts) on one GPU at once, with continuous batching.
  *
  * A server owns one worker thread.  Submitted requests wait in a FIFO queue
- * and are admitted between RK4 steps while their device footprint
- * (mmvm_request_footprint) fits the HBM budget; admitted simulations keep
- * their state on the device and advance one RK4 step per tick together (one
- * graph-captured tick: per order, a persistent all-pairs launch over every
- * admitted simulation of that order); a simulation leaves the batch at the
- * end of the tick in which it completes nsteps.  The result of a request
- * does not depend on the other requests in the batch (the split of its pairs
- * into work items depends on its own size only).  The far field is not used
- * (every pair takes the full jet).  Submit, poll and stats are thread-safe.
+ * and are admitted while their device footprint (mmvm_request_footprint)
+ * fits the HBM budget; admitted simulations keep their state on the device.
+ * Simulations of one order and size class form a batch that advances one
+ * RK4 step per tick (a graph-captured tick: a persistent all-pairs launch
+ * over every member, batched records and finish); batches tick
+ * independently on their own streams, members join and leave between ticks,
+ * and a simulation leaves at the end of the tick in which it completes
+ * nsteps.  The result of a request does not depend on the other requests
+ * (its work split and spatial order depend on its own state only).  FP32
+ * servers use the far field unless flags holds MMVM_FLAG_NO_FAR_FIELD.
+ * Submit, poll and stats are thread-safe.
  * ---------------------------------------------------------------------- */
 typedef struct mmvm_server mmvm_server;
 
@@ -217,8 +219,8 @@ typedef struct {
   int32_t precision;         /* MMVM_FP64 or MMVM_MIXED_FP32, every request  */
   uint64_t hbm_budget_bytes; /* admission budget; 0: half the free device
                                 memory at creation                          */
-  int32_t max_active;        /* most simulations in one tick; 0: 256         */
-  uint32_t flags;            /* reserved, must be 0                          */
+  int32_t max_active;        /* most simulations admitted at once; 0: 256    */
+  uint32_t flags;            /* 0 or MMVM_FLAG_NO_FAR_FIELD                  */
 } mmvm_server_config;
 
 /* One simulation: the state of eq:vorticity_decomposition at t0 (layouts as
@@ -249,10 +251,11 @@ typedef struct {
 
 typedef struct {
   int64_t submitted, completed, failed, queued, active;
-  int64_t ticks;             /* RK4 steps of the batch                       */
-  int64_t max_batch;         /* most simulations in one tick                 */
+  int64_t ticks;             /* batch ticks (one RK4 step of a batch)        */
+  int64_t max_batch;         /* most simulations in one batch tick           */
+  int64_t max_active;        /* most simulations admitted at once            */
   double pair_interactions;  /* sum over ticks of 4 sum_i n_i^2              */
-  double busy_ms;            /* host wall time of the ticks                  */
+  double busy_ms;            /* host wall time with a tick on the GPU        */
   uint64_t footprint_bytes;  /* admitted footprint now                       */
   uint64_t peak_footprint_bytes;
   uint64_t budget_bytes;

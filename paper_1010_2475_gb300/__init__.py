@@ -94,7 +94,8 @@ class mmvm_server_counters(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("active", ctypes.c_int64), ("ticks", ctypes.c_int64),
-                ("max_batch", ctypes.c_int64), ("pair_interactions", ctypes.c_double),
+                ("max_batch", ctypes.c_int64), ("max_active", ctypes.c_int64),
+                ("pair_interactions", ctypes.c_double),
                 ("busy_ms", ctypes.c_double), ("footprint_bytes", ctypes.c_uint64),
                 ("peak_footprint_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64)]
 
@@ -362,9 +363,9 @@ class Server:
     poll for their final states."""
 
     def __init__(self, precision: int = MMVM_MIXED_FP32, device: int = 0,
-                 hbm_budget_bytes: int = 0, max_active: int = 0):
+                 hbm_budget_bytes: int = 0, max_active: int = 0, flags: int = 0):
         self.handle = ctypes.c_void_p()
-        cfg = mmvm_server_config(device, precision, hbm_budget_bytes, max_active, 0)
+        cfg = mmvm_server_config(device, precision, hbm_budget_bytes, max_active, flags)
         _check(load_library().mmvm_server_create(ctypes.byref(cfg), ctypes.byref(self.handle)))
         self._orders = {}
 

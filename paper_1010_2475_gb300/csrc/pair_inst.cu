@@ -35,10 +35,11 @@ cudaError_t prepare_fn(int S) {
                               (int)smem_fn(S));
 }
 cudaError_t launch_batch_fn(const void* rec, const BatchInst* inst, const int4* items,
-                            const int* n_items, int* counter, int grid, int S, double* partial,
-                            cudaStream_t st) {
+                            const int* n_items, int* counter, int grid, int S, const void* gbox,
+                            double* partial, cudaStream_t st) {
   MMVM_BATCH_KERNEL<<<grid, kTPC, smem_fn(S), st>>>(static_cast<const T*>(rec), inst, items,
-                                                    n_items, counter, S, partial);
+                                                    n_items, counter, S,
+                                                    static_cast<const float4*>(gbox), partial);
   return cudaGetLastError();
 }
 cudaError_t occ_batch_fn(int S, int* blocks) {

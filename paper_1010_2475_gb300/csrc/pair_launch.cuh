@@ -264,12 +264,15 @@ __global__ void __launch_bounds__(TPC, MINB)
 // Many independent instances of one order in one persistent launch: every
 // CTA takes work items (instance, target tile, source chunk) from a shared
 // counter until none is left.  Items are listed by the host, costliest first.
-// The counter must be zero at launch (the caller clears it).
+// The counter must be zero at launch (the caller clears it).  gbox (null: no
+// far field) holds the group boxes of the whole batch (instances start on
+// group boundaries).
 template <int M, typename T, int LO, int HI, int TPC, int MINB, bool SYNC>
 __global__ void __launch_bounds__(TPC, MINB)
     pair_batch_kernel(const T* __restrict__ rec, const BatchInst* __restrict__ inst,
                       const int4* __restrict__ items, const int* __restrict__ n_items,
-                      int* __restrict__ counter, int S, double* __restrict__ partial) {
+                      int* __restrict__ counter, int S, const float4* __restrict__ gbox,
+                      double* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int item_s;
   constexpr int NB = n_beta(M);
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(TPC, MINB)
     const int c0 = w.z * ip.chunk_len;
     const int c1 = min(ip.n, c0 + ip.chunk_len);
     pair_tile_work<M, T, LO, HI, TPC, SYNC>(rec + (size_t)ip.slot0 * R, ip.n, w.y, c0, c1, S,
-                                            nullptr,
+                                            gbox ? gbox + ip.slot0 / kGroup : nullptr,
                                             partial + ip.part_off + (size_t)w.z * NB * ip.n,
                                             nullptr, smem_raw);
   }

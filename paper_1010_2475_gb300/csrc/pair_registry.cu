@@ -164,10 +164,10 @@ int pair_batch_occupancy(const PairEntry& e, int S) {
 
 cudaError_t pair_launch_batch(const PairEntry& e, const void* rec, const BatchInst* inst,
                               const int4* items, const int* n_items, int* counters, int grid,
-                              int S, double* partial, cudaStream_t st) {
+                              int S, const void* gbox, double* partial, cudaStream_t st) {
   for (int s = 0; s < e.nslices; ++s) {
     cudaError_t r = e.slices[s].launch_batch(rec, inst, items, n_items, counters + s, grid, S,
-                                             partial, st);
+                                             gbox, partial, st);
     if (r != cudaSuccess) return r;
   }
   return cudaSuccess;

@@ -19,7 +19,7 @@ struct SliceEntry {
   cudaError_t (*occupancy)(int S, int* blocks_per_sm) = nullptr;
   // persistent batched form (pair_batch_kernel): `grid` CTAs
   cudaError_t (*launch_batch)(const void* rec, const BatchInst* inst, const int4* items,
-                              const int* n_items, int* counter, int grid, int S,
+                              const int* n_items, int* counter, int grid, int S, const void* gbox,
                               double* partial, cudaStream_t st) = nullptr;
   cudaError_t (*occupancy_batch)(int S, int* blocks_per_sm) = nullptr;
 };
@@ -57,9 +57,10 @@ cudaError_t pair_launch(const PairEntry& e, const void* rec, int n, int chunks, 
 // CTAs per SM of the batched slice kernels (the smallest), 0 on error.
 int pair_batch_occupancy(const PairEntry& e, int S);
 // Launch every slice of the batched form, `grid` persistent CTAs each;
-// counters[s] (zero at launch) hands out the items to slice s.
+// counters[s] (zero at launch) hands out the items to slice s; gbox (null:
+// no far field) holds the batch's group boxes.
 cudaError_t pair_launch_batch(const PairEntry& e, const void* rec, const BatchInst* inst,
                               const int4* items, const int* n_items, int* counters, int grid,
-                              int S, double* partial, cudaStream_t st);
+                              int S, const void* gbox, double* partial, cudaStream_t st);
 
 }  // namespace mmvm

@@ -255,19 +255,43 @@ __device__ __forceinline__ const double* inst_stage_m(const BatchInst& I, int K,
 // instance slot_inst[p / kGroup]; padding slots past an instance's n are not
 // written (no kernel reads them).  src = 0 reads the step-start state y,
 // src = 1 the stage state ys; the core is taken at t + cs dt of each instance.
+// With perm_local, sorted slot p holds local particle perm_local[p]; with
+// gbox, every warp (one group of kGroup slots: the loop keeps warps aligned
+// to groups and n_slots is a multiple of kGroup) writes its group's box.
 template <typename T>
 __global__ void prep_batch_kernel(int M, int K, int R, const BatchInst* __restrict__ inst,
                                   const int* __restrict__ slot_inst,
                                   const int* __restrict__ n_slots, int src, double cs,
-                                  T* __restrict__ rec) {
+                                  const int* __restrict__ perm_local, T* __restrict__ rec,
+                                  float4* __restrict__ gbox) {
   const int total = *n_slots;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += gridDim.x * blockDim.x) {
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    const int p = base + threadIdx.x;  // whole warps are in or out of range
+    if (p >= total) continue;
     const BatchInst& I = inst[slot_inst[p / kGroup]];
     const int j = p - I.slot0;
-    if (j >= I.n) continue;
-    const double c = 2.0 * (I.lam0sq + I.four_nu * (I.t + cs * I.dt));
-    make_record<T>(rec + (size_t)p * R, inst_stage_x(I, K, src) + 2 * j,
-                   inst_stage_m(I, K, src) + (size_t)j * K, M, K, R, 1.0 / sqrt(c));
+    float lo1 = 3.4e38f, hi1 = -3.4e38f, lo2 = 3.4e38f, hi2 = -3.4e38f;
+    if (j < I.n) {
+      const int jj = perm_local ? perm_local[p] : j;
+      const double c = 2.0 * (I.lam0sq + I.four_nu * (I.t + cs * I.dt));
+      T* r = rec + (size_t)p * R;
+      make_record<T>(r, inst_stage_x(I, K, src) + 2 * jj, inst_stage_m(I, K, src) + (size_t)jj * K,
+                     M, K, R, 1.0 / sqrt(c));
+      if constexpr (sizeof(T) == 4) {
+        lo1 = hi1 = r[0];
+        lo2 = hi2 = r[1];
+      }
+    }
+    if (gbox) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+        hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+        lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+        hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+      }
+      if ((threadIdx.x & 31) == 0) gbox[p / kGroup] = make_float4(lo1, hi1, lo2, hi2);
+    }
   }
 }
 
@@ -288,7 +312,7 @@ __global__ void finish_batch_kernel(BatchFinishArgs B) {
     A.nchunks = I.n > 1 ? I.chunks : 0;
     A.targets_per_block = B.targets_per_block;
     A.partial = I.n > 1 ? B.partial + I.part_off : nullptr;
-    A.perm = nullptr;
+    A.perm = B.perm_local ? B.perm_local + I.slot0 : nullptr;
     A.Min = inst_stage_m(I, B.K, B.src);
     A.k_off = B.k_off;
     A.e_l = B.e_l;
@@ -341,17 +365,18 @@ cudaError_t launch_scan_batch(int M, const BatchInst* inst, const int* n_inst, i
 }
 
 cudaError_t launch_prep_batch(int precision, int M, const BatchInst* inst, const int* slot_inst,
-                              const int* n_slots, int max_slots, int src, double cs, void* rec,
-                              cudaStream_t st) {
+                              const int* n_slots, int max_slots, int src, double cs,
+                              const int* perm_local, void* rec, void* gbox, cudaStream_t st) {
   const int K = n_moments(M);
   const int threads = 128, blocks = std::max(1, std::min((max_slots + threads - 1) / threads, 4096));
   if (precision == 1)
     prep_batch_kernel<float><<<blocks, threads, 0, st>>>(M, K, rec_len<float>(M), inst, slot_inst,
-                                                         n_slots, src, cs, (float*)rec);
+                                                         n_slots, src, cs, perm_local,
+                                                         (float*)rec, (float4*)gbox);
   else
     prep_batch_kernel<double><<<blocks, threads, 0, st>>>(M, K, rec_len<double>(M), inst,
-                                                          slot_inst, n_slots, src, cs,
-                                                          (double*)rec);
+                                                          slot_inst, n_slots, src, cs, perm_local,
+                                                          (double*)rec, nullptr);
   return cudaGetLastError();
 }
 

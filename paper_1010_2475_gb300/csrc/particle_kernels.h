@@ -44,6 +44,7 @@ struct BatchFinishArgs {
   const int2* items = nullptr;
   const int* n_items = nullptr;     // device count of items
   const double* partial = nullptr;  // the batch's partials (BatchInst::part_off)
+  const int* perm_local = nullptr;  // batch order (null: identity)
   const int* k_off = nullptr;       // finish tables of the order (tables.h)
   const int* e_l = nullptr;
   const int* e_b = nullptr;
@@ -54,9 +55,20 @@ struct BatchFinishArgs {
   int mode = 1;
 };
 
+// perm_local (nullable): sorted slot -> local particle index (batch order);
+// gbox (nullable): float4 box per group of kGroup slots (FP32 records only).
 cudaError_t launch_prep_batch(int precision, int M, const BatchInst* inst, const int* slot_inst,
-                              const int* n_slots, int max_slots, int src, double cs, void* rec,
-                              cudaStream_t st);
+                              const int* n_slots, int max_slots, int src, double cs,
+                              const int* perm_local, void* rec, void* gbox, cudaStream_t st);
+// Spatial order of every instance of a batch (per-instance Morton keys in
+// the instance's own bounding box, one stable 64-bit radix sort over the
+// batch): perm_local[p] = the local particle at sorted slot p.
+size_t batch_order_temp_bytes(int slot_cap);
+cudaError_t launch_batch_order(int slot_cap, const int* n_slots, const BatchInst* inst,
+                               const int* n_inst, int inst_cap, const int* slot_inst, void* ibox,
+                               unsigned long long* kin, unsigned long long* kout, int* iin,
+                               int* iout, void* temp, size_t temp_bytes, int* perm_local,
+                               cudaStream_t st);
 size_t finish_smem_bytes(int M, int targets_per_block);
 // flags[i] = 1 if instance i's step-start state holds a non-finite value.
 cudaError_t launch_scan_batch(int M, const BatchInst* inst, const int* n_inst, int max_inst,

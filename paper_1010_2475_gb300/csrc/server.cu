@@ -3,23 +3,28 @@
 // counts) on one GPU at once.
 //
 // * Continuous batching.  Requests wait in a FIFO queue and are admitted
-//   between steps while their device footprint (state, source records,
-//   partial sums) fits the server's HBM budget; a finished simulation leaves
-//   at the end of the step in which it completes and frees its footprint for
-//   the next one.  Admitted state stays resident on the device until then.
-// * One tick = one RK4 step of every admitted simulation.  Simulations of one
-//   order form a batch: its records, partials and work lists live in buffers
-//   of the batch, and each RK4 stage is three launches for the whole batch
-//   (records, the persistent all-pairs kernel working through a list of
-//   (simulation, target tile, source chunk) items, the FP64 finish).  Batches
-//   of different orders run on their own streams, so their work overlaps.
-//   The tick is captured once as a CUDA graph and replayed; the kernels read
-//   the sizes of the batch from device memory, so admitting or retiring a
-//   simulation only re-uploads the work lists (the graph is captured again
-//   only when a buffer grows or an order appears or disappears).
-// * The way a simulation's pairs are split into items depends on its own
-//   size only, and every item is summed in a fixed order, so a simulation's
-//   result does not depend on what else is in the batch.
+//   while their device footprint (state, source records, partial sums, work
+//   lists) fits the server's HBM budget; admitted state stays resident on the
+//   device until the simulation ends, and a finished simulation frees its
+//   footprint for the next request at once.
+// * Batches.  Admitted simulations of one order and one size class (n up to
+//   256, 1024, 4096, larger) form a batch: its records, partials and work
+//   lists live in buffers of the batch, and one tick of the batch is one RK4
+//   step of all its simulations: per stage three launches for the whole batch
+//   (records; the persistent all-pairs kernel working through a list of
+//   (simulation, target tile, source chunk) items; the FP64 finish), then the
+//   time advance and a divergence scan.  A tick is a CUDA graph, captured
+//   once and replayed; the kernels read the sizes of the batch from device
+//   memory, so a change of members only re-uploads the work lists.
+// * Batches tick independently, each on its own stream: a cheap batch (low
+//   order, small n) is not held back by an expensive one, and the GPU runs
+//   the ticks of different batches at the same time.  Members join and leave
+//   a batch between its ticks.
+// * The split of a simulation's pairs into items and its spatial order
+//   depend on its own state only, and every item is summed in a fixed order,
+//   so a simulation's result does not depend on the rest of its batch.
+// * FP32 batches use the far-field path of the all-pairs kernel, with a
+//   Morton order of each simulation's centres in its own bounding box.
 // * The all-pairs variant of each order is chosen once per process by timing
 //   every compiled variant on the first batch of that order.
 #include <cuda_runtime.h>
@@ -67,6 +72,8 @@ int fail(int code, const std::string& m) {
 constexpr int kChunkTarget = 1024;  // sources per chunk (items of similar cost)
 constexpr int kMaxChunks = 16;
 constexpr int kStages = 4;
+constexpr int kCountHdr = 4;  // n_slots, n_pair_items, n_finish_items, n_inst
+constexpr int kCounters = kStages * mmvm::kMaxSlices;
 
 int chunks_for(int64_t n) {
   if (n <= 1) return 0;
@@ -78,6 +85,8 @@ int chunk_len_for(int64_t n, int chunks) {
 }
 
 int finish_tb(int K) { return std::max(1, 128 / (((K + 31) / 32) * 32)); }
+
+int size_class(int64_t n) { return n <= 256 ? 0 : n <= 1024 ? 1 : n <= 4096 ? 2 : 3; }
 
 size_t rec_bytes(int M, int precision) {
   return precision == MMVM_MIXED_FP32 ? (size_t)mmvm::rec_len<float>(M) * 4
@@ -93,14 +102,17 @@ uint64_t footprint(int M, int precision, int64_t n) {
   const uint64_t part = (uint64_t)chunks_for(n) * NB * n * 8;
   const uint64_t items = (slots / 32 + 1) * (uint64_t)std::max(chunks_for(n), 1) * 16 +
                          (uint64_t)n * 8 + slots / kGroup * 4 + sizeof(BatchInst);
-  return state + recs + part + items;
+  // spatial order of FP32 batches: sorted index, keys and values twice,
+  // group boxes, the simulation's box
+  const uint64_t order = precision == MMVM_MIXED_FP32 ? slots * 28 + slots / kGroup * 16 + 32 : 0;
+  return state + recs + part + items + order;
 }
 
 template <typename T>
 struct DBuf {
   T* p = nullptr;
   size_t cap = 0;
-  // grow to at least n elements (contents are not kept); true if reallocated
+  // at least n elements (contents are not kept); *grown is set on reallocation
   cudaError_t ensure(size_t n, bool* grown) {
     if (p && n <= cap) return cudaSuccess;
     if (p) cudaFree(p);
@@ -135,11 +147,13 @@ struct Request {
   double* d_state = nullptr;  // worker thread only
 };
 
-// Every admitted simulation of one order.
+// Every admitted simulation of one order and size class.
 struct Batch {
   int M = 0, K = 0, NB = 0, tb = 1;
   mmvm::PairEntry pe;  // pe.M == -1: no pair kernel (orders above the pair limit: n == 1 only)
-  std::vector<Request*> members;
+  bool far = false;
+  std::vector<Request*> members;   // in the work lists
+  std::vector<Request*> incoming;  // admitted, state on its way, joining at the next tick
   bool dirty = true;
   bool tuned = false;
   DBuf<int> k_off, e_l, e_b;
@@ -150,33 +164,47 @@ struct Batch {
   DBuf<int> slot_inst;
   DBuf<int4> pitems;
   DBuf<int2> fitems;
-  DBuf<int> counts;  // n_slots, n_pair_items, n_finish_items, n_inst, then the item counters
-  DBuf<int> bad;     // per instance: non-finite state after the tick
+  DBuf<int> counts;  // kCountHdr sizes, then the item counters
+  DBuf<int> bad;     // per simulation: non-finite state after the tick
+  DBuf<float> gbox;  // far field: float4 per group of kGroup slots
+  DBuf<int> perm, iin, iout;
+  DBuf<unsigned long long> kin, kout;
+  DBuf<double> ibox;
+  DBuf<unsigned char> sort_tmp;
   std::vector<int> bad_host;
-  int slot_cap = 0;  // slots the prep grid covers
-  cudaStream_t side = nullptr;
-  int64_t pairs_per_rhs = 0;  // sum of n^2
+  int slot_cap = 0;  // slots every slot-sized buffer holds
+  int inst_cap = 0;  // simulations every per-simulation buffer holds
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr, ev0 = nullptr, ev1 = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_valid = false;
+  bool in_flight = false;
+  int grid = 1;               // persistent CTAs of the pair kernel
+  int64_t pairs_per_rhs = 0;  // sum of n^2 over the members
   void release() {
-    k_off.release();
-    e_l.release();
-    e_b.release();
+    for (auto* b : {&k_off, &e_l, &e_b, &slot_inst, &counts, &bad, &perm, &iin, &iout})
+      b->release();
     e_c.release();
     psi0.release();
     rec.release();
     partial.release();
     inst.release();
-    slot_inst.release();
     pitems.release();
     fitems.release();
-    counts.release();
-    bad.release();
-    if (side) cudaStreamDestroy(side);
-    side = nullptr;
+    gbox.release();
+    kin.release();
+    kout.release();
+    ibox.release();
+    sort_tmp.release();
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (cudaEvent_t* ev : {&done, &ev0, &ev1})
+      if (*ev) cudaEventDestroy(*ev);
+    done = ev0 = ev1 = nullptr;
+    if (st) cudaStreamDestroy(st);
+    st = nullptr;
   }
 };
-
-constexpr int kCountHdr = 4;
-constexpr int kCounters = kStages * mmvm::kMaxSlices;
 
 std::mutex g_batch_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_batch_tuned;  // (device, order, precision) -> variant
@@ -197,16 +225,15 @@ struct mmvm_server {
   std::string broken_msg;
   uint64_t fp_used = 0, fp_peak = 0;
   int64_t n_active = 0, submitted = 0, completed = 0, failed = 0, ticks = 0, max_batch = 0;
+  int64_t max_active = 0;
   double pair_interactions = 0, busy_ms = 0;
   std::thread worker;
   // worker-thread state
-  cudaStream_t st = nullptr;
-  cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr;
-  std::vector<cudaEvent_t> join;
-  std::map<int, Batch> batches;
-  cudaGraphExec_t exec = nullptr;
-  bool graph_valid = false;
-  std::vector<int> graph_orders;
+  cudaStream_t up = nullptr;       // uploads of admitted state
+  cudaEvent_t up_done = nullptr;   // after the latest upload
+  std::map<int, Batch> batches;    // key: order * 4 + size class
+  int in_flight = 0;
+  Clock::time_point busy_since;
 };
 
 namespace {
@@ -224,7 +251,7 @@ void finish_request(mmvm_server* s, Request* r, int status, const std::string& e
     s->failed += 1;
 }
 
-cudaError_t upload_tables(Batch& b, cudaStream_t st) {
+cudaError_t upload_tables(Batch& b) {
   mmvm::FinishTables T = mmvm::build_finish_tables(b.M);
   bool g = false;
   cudaError_t e;
@@ -235,7 +262,7 @@ cudaError_t upload_tables(Batch& b, cudaStream_t st) {
       (e = b.psi0.ensure(T.psi0.size(), &g)) != cudaSuccess)
     return e;
   auto up = [&](void* d, const void* h, size_t bytes) {
-    return bytes ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    return bytes ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, b.st) : cudaSuccess;
   };
   if ((e = up(b.k_off.p, T.k_off.data(), T.k_off.size() * sizeof(int))) != cudaSuccess ||
       (e = up(b.e_l.p, T.e_l.data(), T.e_l.size() * sizeof(int))) != cudaSuccess ||
@@ -243,11 +270,49 @@ cudaError_t upload_tables(Batch& b, cudaStream_t st) {
       (e = up(b.e_c.p, T.e_c.data(), T.e_c.size() * sizeof(double))) != cudaSuccess ||
       (e = up(b.psi0.p, T.psi0.data(), T.psi0.size() * sizeof(double))) != cudaSuccess)
     return e;
-  return cudaStreamSynchronize(st);  // the host tables go out of scope
+  return cudaStreamSynchronize(b.st);  // the host tables go out of scope
 }
 
-// Work lists and descriptors of a batch for the current members.
-cudaError_t rebuild(mmvm_server* s, Batch& b, bool* grown) {
+// Grow every slot-sized and per-simulation buffer to hold `slots` slots and
+// `ninst` simulations (with room to spare).
+cudaError_t ensure_caps(Batch& b, int slots, int ninst, bool* grown) {
+  cudaError_t e = cudaSuccess;
+  const int eb = b.pe.M >= 0 ? b.pe.elem_bytes : 8;
+  const int R = b.pe.M >= 0 ? b.pe.rec_len : mmvm::rec_len<double>(b.M);
+  if (slots > b.slot_cap || !b.rec.p) {
+    const int cap = mmvm::round_up(std::max(slots + slots / 4, kGroup), kGroup);
+    bool g = false;
+    if ((e = b.rec.ensure((size_t)cap * R * eb, &g)) != cudaSuccess ||
+        (e = b.slot_inst.ensure(cap / kGroup, &g)) != cudaSuccess)
+      return e;
+    if (b.far) {
+      const size_t sb = mmvm::batch_order_temp_bytes(cap);
+      if ((e = b.gbox.ensure((size_t)4 * (cap / kGroup), &g)) != cudaSuccess ||
+          (e = b.perm.ensure(cap, &g)) != cudaSuccess ||
+          (e = b.iin.ensure(cap, &g)) != cudaSuccess ||
+          (e = b.iout.ensure(cap, &g)) != cudaSuccess ||
+          (e = b.kin.ensure(cap, &g)) != cudaSuccess ||
+          (e = b.kout.ensure(cap, &g)) != cudaSuccess ||
+          (e = b.sort_tmp.ensure(sb, &g)) != cudaSuccess)
+        return e;
+    }
+    b.slot_cap = cap;
+    *grown = true;
+  }
+  if (ninst > b.inst_cap || !b.inst.p) {
+    const int cap = std::max(ninst + ninst / 4, 8);
+    bool g = false;
+    if ((e = b.inst.ensure(cap, &g)) != cudaSuccess || (e = b.bad.ensure(cap, &g)) != cudaSuccess)
+      return e;
+    if (b.far && (e = b.ibox.ensure((size_t)4 * cap, &g)) != cudaSuccess) return e;
+    b.inst_cap = cap;
+    *grown = true;
+  }
+  return e;
+}
+
+// Work lists and descriptors of a batch for its current members.
+cudaError_t rebuild(Batch& b, bool* grown) {
   std::vector<BatchInst> inst;
   std::vector<int> slot_inst;
   std::vector<std::pair<int64_t, int4>> pit;
@@ -294,25 +359,15 @@ cudaError_t rebuild(mmvm_server* s, Batch& b, bool* grown) {
   std::vector<int4> pitems(pit.size());
   for (size_t i = 0; i < pit.size(); ++i) pitems[i] = pit[i].second;
   cudaError_t e;
-  const int eb = b.pe.M >= 0 ? b.pe.elem_bytes : 8;
-  const int R = b.pe.M >= 0 ? b.pe.rec_len : mmvm::rec_len<double>(b.M);
-  if ((e = b.rec.ensure((size_t)std::max(slots, kGroup) * R * eb, grown)) != cudaSuccess ||
+  if ((e = ensure_caps(b, slots, (int)inst.size(), grown)) != cudaSuccess ||
       (e = b.partial.ensure((size_t)std::max<long long>(part, 1), grown)) != cudaSuccess ||
-      (e = b.inst.ensure(std::max<size_t>(inst.size(), 1), grown)) != cudaSuccess ||
-      (e = b.slot_inst.ensure(std::max<size_t>(slot_inst.size(), 1), grown)) != cudaSuccess ||
       (e = b.pitems.ensure(std::max<size_t>(pitems.size(), 1), grown)) != cudaSuccess ||
       (e = b.fitems.ensure(std::max<size_t>(fit.size(), 1), grown)) != cudaSuccess ||
-      (e = b.counts.ensure(kCountHdr + kCounters, grown)) != cudaSuccess ||
-      (e = b.bad.ensure(std::max<size_t>(inst.size(), 1), grown)) != cudaSuccess)
+      (e = b.counts.ensure(kCountHdr + kCounters, grown)) != cudaSuccess)
     return e;
-  const int slot_cap = (int)(b.rec.cap / ((size_t)R * eb));
-  if (slot_cap != b.slot_cap) {
-    b.slot_cap = slot_cap;
-    *grown = true;
-  }
   const int hdr[kCountHdr] = {slots, (int)pitems.size(), (int)fit.size(), (int)inst.size()};
   auto up = [&](void* d, const void* h, size_t bytes) {
-    return bytes ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s->st) : cudaSuccess;
+    return bytes ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, b.st) : cudaSuccess;
   };
   if ((e = up(b.inst.p, inst.data(), inst.size() * sizeof(BatchInst))) != cudaSuccess ||
       (e = up(b.slot_inst.p, slot_inst.data(), slot_inst.size() * sizeof(int))) != cudaSuccess ||
@@ -320,35 +375,43 @@ cudaError_t rebuild(mmvm_server* s, Batch& b, bool* grown) {
       (e = up(b.fitems.p, fit.data(), fit.size() * sizeof(int2))) != cudaSuccess ||
       (e = up(b.counts.p, hdr, sizeof(hdr))) != cudaSuccess)
     return e;
-  // pageable sources: the copies are complete before the vectors go
-  e = cudaStreamSynchronize(s->st);
+  e = cudaStreamSynchronize(b.st);  // the host vectors go out of scope
   b.dirty = false;
   return e;
 }
 
-int pair_grid(mmvm_server* s, const Batch& b) {
+// Persistent CTAs of the batch's pair kernel (queried outside any capture).
+int pair_grid(const mmvm_server* s, const Batch& b) {
   const int per_sm = std::max(1, mmvm::pair_batch_occupancy(b.pe, kGroup));
   return s->sms * per_sm;
 }
 
-// One RK4 step of a batch on stream st (captured into the tick graph).
-cudaError_t enqueue_batch_step(mmvm_server* s, Batch& b, cudaStream_t st) {
+// One RK4 step of a batch on its stream (captured into its tick graph).
+cudaError_t enqueue_batch_step(const mmvm_server* s, Batch& b) {
   cudaError_t e;
   const int prec = s->cfg.precision;
+  cudaStream_t st = b.st;
   int* counters = b.counts.p + kCountHdr;
   if ((e = cudaMemsetAsync(counters, 0, kCounters * sizeof(int), st)) != cudaSuccess) return e;
+  const bool pairs = b.pe.M >= 0;
+  const bool far = pairs && b.far;
+  if (far && (e = mmvm::launch_batch_order(b.slot_cap, b.counts.p, b.inst.p, b.counts.p + 3,
+                                           b.inst_cap, b.slot_inst.p, b.ibox.p, b.kin.p, b.kout.p,
+                                           b.iin.p, b.iout.p, b.sort_tmp.p, b.sort_tmp.cap,
+                                           b.perm.p, st)) != cudaSuccess)
+    return e;
   static const double cs[kStages] = {0.0, 0.5, 0.5, 1.0};
   const int fgrid = std::max(1, std::min(s->sms * 4, (b.slot_cap + b.tb - 1) / b.tb));
   for (int stage = 1; stage <= kStages; ++stage) {
     const int src = stage == 1 ? 0 : 1;
-    if (b.pe.M >= 0) {
+    if (pairs) {
       if ((e = mmvm::launch_prep_batch(prec, b.M, b.inst.p, b.slot_inst.p, b.counts.p,
-                                       b.slot_cap, src, cs[stage - 1], b.rec.p, st)) !=
-          cudaSuccess)
+                                       b.slot_cap, src, cs[stage - 1], far ? b.perm.p : nullptr,
+                                       b.rec.p, far ? b.gbox.p : nullptr, st)) != cudaSuccess)
         return e;
       if ((e = mmvm::pair_launch_batch(b.pe, b.rec.p, b.inst.p, b.pitems.p, b.counts.p + 1,
-                                       counters + (stage - 1) * mmvm::kMaxSlices,
-                                       pair_grid(s, b), kGroup, b.partial.p, st)) != cudaSuccess)
+                                       counters + (stage - 1) * mmvm::kMaxSlices, b.grid, kGroup,
+                                       far ? b.gbox.p : nullptr, b.partial.p, st)) != cudaSuccess)
         return e;
     }
     mmvm::BatchFinishArgs B;
@@ -360,6 +423,7 @@ cudaError_t enqueue_batch_step(mmvm_server* s, Batch& b, cudaStream_t st) {
     B.items = b.fitems.p;
     B.n_items = b.counts.p + 2;
     B.partial = b.partial.p;
+    B.perm_local = far ? b.perm.p : nullptr;
     B.k_off = b.k_off.p;
     B.e_l = b.e_l.p;
     B.e_b = b.e_b.p;
@@ -370,55 +434,36 @@ cudaError_t enqueue_batch_step(mmvm_server* s, Batch& b, cudaStream_t st) {
     B.mode = stage;
     if ((e = mmvm::launch_finish_batch(B, fgrid, st)) != cudaSuccess) return e;
   }
-  if ((e = mmvm::launch_advance_batch(b.inst.p, b.counts.p + 3, (int)b.inst.cap, st)) !=
-      cudaSuccess)
+  if ((e = mmvm::launch_advance_batch(b.inst.p, b.counts.p + 3, b.inst_cap, st)) != cudaSuccess)
     return e;
   // divergence check: a simulation whose state left the finite range stops
-  return mmvm::launch_scan_batch(b.M, b.inst.p, b.counts.p + 3, (int)b.inst.cap, b.bad.p, st);
+  return mmvm::launch_scan_batch(b.M, b.inst.p, b.counts.p + 3, b.inst_cap, b.bad.p, st);
 }
 
-cudaError_t capture_tick(mmvm_server* s) {
-  if (s->exec) {
-    cudaGraphExecDestroy(s->exec);
-    s->exec = nullptr;
+cudaError_t capture_batch(const mmvm_server* s, Batch& b) {
+  if (b.exec) {
+    cudaGraphExecDestroy(b.exec);
+    b.exec = nullptr;
   }
-  s->graph_orders.clear();
-  cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e = cudaStreamBeginCapture(b.st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  cudaError_t ee = cudaEventRecord(s->fork, s->st);
-  size_t gi = 0;
-  for (auto& kv : s->batches) {
-    Batch& b = kv.second;
-    if (b.members.empty() || ee != cudaSuccess) continue;
-    if (gi >= s->join.size()) {
-      cudaEvent_t ev;
-      ee = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-      if (ee != cudaSuccess) break;
-      s->join.push_back(ev);
-    }
-    if ((ee = cudaStreamWaitEvent(b.side, s->fork, 0)) != cudaSuccess) break;
-    if ((ee = enqueue_batch_step(s, b, b.side)) != cudaSuccess) break;
-    if ((ee = cudaEventRecord(s->join[gi], b.side)) != cudaSuccess) break;
-    if ((ee = cudaStreamWaitEvent(s->st, s->join[gi], 0)) != cudaSuccess) break;
-    s->graph_orders.push_back(kv.first);
-    ++gi;
-  }
+  const cudaError_t ee = enqueue_batch_step(s, b);
   cudaGraph_t g = nullptr;
-  e = cudaStreamEndCapture(s->st, &g);
+  e = cudaStreamEndCapture(b.st, &g);
   if (ee != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return ee;
   }
   if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(&s->exec, g, 0);
+  e = cudaGraphInstantiate(&b.exec, g, 0);
   cudaGraphDestroy(g);
-  if (e == cudaSuccess) s->graph_valid = true;
+  if (e == cudaSuccess) b.graph_valid = true;
   return e;
 }
 
-// Time every compiled variant of a batch on its first members (stage-1
-// records) and keep the fastest, once per (device, order, precision).
-cudaError_t tune_batch(mmvm_server* s, Batch& b) {
+// Time every compiled variant of a batch's order on its first members
+// (stage-1 records) and keep the fastest, once per (device, order, precision).
+cudaError_t tune_batch(const mmvm_server* s, Batch& b) {
   b.tuned = true;
   const int nv = mmvm::pair_variant_count(b.M, s->cfg.precision);
   if (nv < 1) return cudaSuccess;
@@ -443,24 +488,24 @@ cudaError_t tune_batch(mmvm_server* s, Batch& b) {
       if ((e = mmvm::pair_prepare(pe, kGroup)) != cudaSuccess) return e;
       b.pe = pe;
       bool grown = false;
-      if ((e = rebuild(s, b, &grown)) != cudaSuccess) return e;
+      if ((e = rebuild(b, &grown)) != cudaSuccess) return e;
       if ((e = mmvm::launch_prep_batch(s->cfg.precision, b.M, b.inst.p, b.slot_inst.p,
-                                       b.counts.p, b.slot_cap, 0, 0.0, b.rec.p, s->st)) !=
-          cudaSuccess)
+                                       b.counts.p, b.slot_cap, 0, 0.0, nullptr, b.rec.p, nullptr,
+                                       b.st)) != cudaSuccess)
         return e;
       float ms = 0.f;
       for (int rep = 0; rep < 2; ++rep) {
         int* counters = b.counts.p + kCountHdr;
-        if ((e = cudaMemsetAsync(counters, 0, kCounters * sizeof(int), s->st)) != cudaSuccess)
+        if ((e = cudaMemsetAsync(counters, 0, kCounters * sizeof(int), b.st)) != cudaSuccess)
           return e;
-        if ((e = cudaEventRecord(s->ev0, s->st)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(b.ev0, b.st)) != cudaSuccess) return e;
         if ((e = mmvm::pair_launch_batch(pe, b.rec.p, b.inst.p, b.pitems.p, b.counts.p + 1,
-                                         counters, pair_grid(s, b), kGroup, b.partial.p,
-                                         s->st)) != cudaSuccess)
+                                         counters, pair_grid(s, b), kGroup, nullptr, b.partial.p,
+                                         b.st)) != cudaSuccess)
           return e;
-        if ((e = cudaEventRecord(s->ev1, s->st)) != cudaSuccess) return e;
-        if ((e = cudaEventSynchronize(s->ev1)) != cudaSuccess) return e;
-        if ((e = cudaEventElapsedTime(&ms, s->ev0, s->ev1)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(b.ev1, b.st)) != cudaSuccess) return e;
+        if ((e = cudaEventSynchronize(b.ev1)) != cudaSuccess) return e;
+        if ((e = cudaEventElapsedTime(&ms, b.ev0, b.ev1)) != cudaSuccess) return e;
       }
       if (const char* vb = std::getenv("MMVM_TUNE_VERBOSE"))
         if (std::atoi(vb))
@@ -480,14 +525,15 @@ cudaError_t tune_batch(mmvm_server* s, Batch& b) {
   if ((e = mmvm::pair_prepare(pe, kGroup)) != cudaSuccess) return e;
   b.pe = pe;
   b.dirty = true;
-  s->graph_valid = false;
+  b.graph_valid = false;
   return cudaSuccess;
 }
 
-Batch& batch_of(mmvm_server* s, int M, cudaError_t* e) {
-  auto it = s->batches.find(M);
+Batch& batch_of(mmvm_server* s, int M, int64_t n, cudaError_t* e) {
+  const int key = M * 4 + size_class(n);
+  auto it = s->batches.find(key);
   if (it != s->batches.end()) return it->second;
-  Batch& b = s->batches[M];
+  Batch& b = s->batches[key];
   b.M = M;
   b.K = mmvm::n_moments(M);
   b.NB = mmvm::n_beta(M);
@@ -497,8 +543,12 @@ Batch& batch_of(mmvm_server* s, int M, cudaError_t* e) {
     b.pe = mmvm::pair_entry(M, s->cfg.precision, 0);
     if (b.pe.M == M) *e = mmvm::pair_prepare(b.pe, kGroup);
   }
-  if (*e == cudaSuccess) *e = cudaStreamCreateWithFlags(&b.side, cudaStreamNonBlocking);
-  if (*e == cudaSuccess) *e = upload_tables(b, s->st);
+  b.far = s->cfg.precision == MMVM_MIXED_FP32 && !(s->cfg.flags & MMVM_FLAG_NO_FAR_FIELD);
+  if (*e == cudaSuccess) *e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
+  if (*e == cudaSuccess) *e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+  if (*e == cudaSuccess) *e = cudaEventCreate(&b.ev0);
+  if (*e == cudaSuccess) *e = cudaEventCreate(&b.ev1);
+  if (*e == cudaSuccess) *e = upload_tables(b);
   return b;
 }
 
@@ -508,7 +558,9 @@ void fail_everything(mmvm_server* s, const std::string& msg) {
   s->broken_msg = msg;
   for (auto& kv : s->batches) {
     for (Request* r : kv.second.members) finish_request(s, r, MMVM_E_DEVICE, msg);
+    for (Request* r : kv.second.incoming) finish_request(s, r, MMVM_E_DEVICE, msg);
     kv.second.members.clear();
+    kv.second.incoming.clear();
   }
   for (Request* r : s->queue) {
     r->status = MMVM_E_DEVICE;
@@ -518,6 +570,82 @@ void fail_everything(mmvm_server* s, const std::string& msg) {
   }
   s->queue.clear();
   s->cv.notify_all();
+}
+
+// Bookkeeping after a batch's tick: advance every member, retire the ones
+// that are done or diverged (state back to the host, device state freed).
+cudaError_t complete_tick(mmvm_server* s, Batch& b) {
+  cudaError_t e;
+  const size_t nm = b.members.size();
+  b.bad_host.assign(nm, 0);
+  if (nm && (e = cudaMemcpyAsync(b.bad_host.data(), b.bad.p, nm * sizeof(int),
+                                 cudaMemcpyDeviceToHost, b.st)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(b.st)) != cudaSuccess) return e;
+  std::vector<Request*> keep;
+  for (size_t i = 0; i < nm; ++i) {
+    Request* r = b.members[i];
+    r->steps_done += 1;
+    r->t = r->t + r->dt;  // the device does the same addition
+    if (r->steps_done < r->nsteps && !b.bad_host[i]) {
+      keep.push_back(r);
+      continue;
+    }
+    e = cudaMemcpyAsync(r->x.data(), r->d_state, r->x.size() * sizeof(double),
+                        cudaMemcpyDeviceToHost, b.st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r->m.data(), r->d_state + 2 * r->n, r->m.size() * sizeof(double),
+                          cudaMemcpyDeviceToHost, b.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b.st);
+    if (e != cudaSuccess) return e;
+    cudaFreeAsync(r->d_state, b.st);
+    r->d_state = nullptr;
+    int status = MMVM_OK;
+    std::string msg;
+    if (b.bad_host[i]) {
+      status = MMVM_E_NUMERIC;
+      msg = "the state left the finite range at step " + std::to_string(r->steps_done);
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    finish_request(s, r, status, msg);
+  }
+  if (keep.size() != nm) {
+    b.members.swap(keep);
+    b.dirty = true;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->ticks += 1;
+  s->pair_interactions += 4.0 * (double)b.pairs_per_rhs;
+  s->max_batch = std::max(s->max_batch, (int64_t)nm);
+  return cudaSuccess;
+}
+
+// Start the next tick of an idle batch (new members join first).
+cudaError_t launch_tick(mmvm_server* s, Batch& b) {
+  cudaError_t e;
+  if (!b.incoming.empty()) {
+    // the state of newcomers is uploaded on the upload stream
+    if ((e = cudaStreamWaitEvent(b.st, s->up_done, 0)) != cudaSuccess) return e;
+    for (Request* r : b.incoming) b.members.push_back(r);
+    b.incoming.clear();
+    b.dirty = true;
+  }
+  if (b.members.empty()) return cudaSuccess;
+  if (!b.tuned && b.pe.M >= 0 && (e = tune_batch(s, b)) != cudaSuccess) return e;
+  if (b.dirty) {
+    bool grown = false;
+    if ((e = rebuild(b, &grown)) != cudaSuccess) return e;
+    if (grown) b.graph_valid = false;
+  }
+  if (!b.graph_valid) {
+    if (b.pe.M >= 0) b.grid = pair_grid(s, b);
+    if ((e = capture_batch(s, b)) != cudaSuccess) return e;
+  }
+  if ((e = cudaGraphLaunch(b.exec, b.st)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(b.done, b.st)) != cudaSuccess) return e;
+  b.in_flight = true;
+  if (s->in_flight++ == 0) s->busy_since = Clock::now();
+  return cudaSuccess;
 }
 
 void worker_main(mmvm_server* s) {
@@ -530,145 +658,86 @@ void worker_main(mmvm_server* s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop) break;
-      while (!s->queue.empty() && s->n_active + (int64_t)admitted.size() < s->cfg.max_active) {
+      while (!s->queue.empty() && s->n_active < s->cfg.max_active) {
         Request* r = s->queue.front();
-        const bool idle = s->n_active == 0 && admitted.empty();
-        if (!idle && s->fp_used + r->fp > s->budget) break;  // FIFO: wait for room
+        if (s->n_active > 0 && s->fp_used + r->fp > s->budget) break;  // FIFO: wait for room
         s->queue.pop_front();
         s->fp_used += r->fp;
         s->fp_peak = std::max(s->fp_peak, s->fp_used);
         s->n_active += 1;
+        s->max_active = std::max(s->max_active, s->n_active);
         r->t_admit = Clock::now();
         admitted.push_back(r);
       }
-      if (s->n_active == 0) {
+      if (s->n_active == 0 && s->in_flight == 0) {
         s->cv.wait_for(lk, std::chrono::milliseconds(20));
         continue;
       }
     }
-    // device state of the newcomers (step-start block y = (x, M))
+    bool progress = !admitted.empty();
+    // newcomers: device state on the upload stream (stream-ordered allocation)
     for (Request* r : admitted) {
+      if (r->nsteps == 0) {  // nothing to integrate: the input is the result
+        std::lock_guard<std::mutex> lk(s->mu);
+        finish_request(s, r, MMVM_OK, "");
+        continue;
+      }
       const int K = mmvm::n_moments(r->order);
-      cudaError_t e = cudaMalloc(&r->d_state, 6 * (size_t)r->n * (2 + K) * sizeof(double));
+      cudaError_t e =
+          cudaMallocAsync(&r->d_state, 6 * (size_t)r->n * (2 + K) * sizeof(double), s->up);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(r->d_state, r->x.data(), r->x.size() * sizeof(double),
-                            cudaMemcpyHostToDevice, s->st);
+                            cudaMemcpyHostToDevice, s->up);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(r->d_state + 2 * r->n, r->m.data(), r->m.size() * sizeof(double),
-                            cudaMemcpyHostToDevice, s->st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+                            cudaMemcpyHostToDevice, s->up);
       if (e != cudaSuccess) {
-        if (r->d_state) cudaFree(r->d_state);
+        if (r->d_state) cudaFreeAsync(r->d_state, s->up);
         r->d_state = nullptr;
         cudaGetLastError();
         std::lock_guard<std::mutex> lk(s->mu);
         finish_request(s, r, e == cudaErrorMemoryAllocation ? MMVM_E_OOM : MMVM_E_DEVICE,
                        std::string("admission: ") + cudaGetErrorString(e));
-        s->cv.notify_all();
-        continue;
-      }
-      if (r->nsteps == 0) {  // nothing to integrate
-        cudaFree(r->d_state);
-        r->d_state = nullptr;
-        std::lock_guard<std::mutex> lk(s->mu);
-        finish_request(s, r, MMVM_OK, "");
-        s->cv.notify_all();
         continue;
       }
       cudaError_t eb = cudaSuccess;
-      Batch& b = batch_of(s, r->order, &eb);
+      Batch& b = batch_of(s, r->order, r->n, &eb);
       if (eb != cudaSuccess) {
         fail_everything(s, std::string("batch set-up: ") + cudaGetErrorString(eb));
         return;
       }
-      b.members.push_back(r);
-      b.dirty = true;
+      b.incoming.push_back(r);
     }
-    // work lists; a new order or a grown buffer needs a new graph
-    std::vector<int> orders;
-    cudaError_t e = cudaSuccess;
-    for (auto& kv : s->batches) {
-      Batch& b = kv.second;
-      if (b.members.empty()) continue;
-      orders.push_back(kv.first);
-      if (!b.tuned && b.pe.M >= 0) e = tune_batch(s, b);
-      if (e != cudaSuccess) break;
-      if (b.dirty) {
-        bool grown = false;
-        e = rebuild(s, b, &grown);
-        if (grown) s->graph_valid = false;
-      }
-      if (e != cudaSuccess) break;
-    }
-    if (e == cudaSuccess && orders.empty()) continue;
-    if (e == cudaSuccess && (!s->graph_valid || orders != s->graph_orders)) e = capture_tick(s);
-    const auto t0 = Clock::now();
-    if (e == cudaSuccess) e = cudaGraphLaunch(s->exec, s->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-    const auto t1 = Clock::now();
-    if (e != cudaSuccess) {
-      fail_everything(s, std::string("tick: ") + cudaGetErrorString(e));
+    if (!admitted.empty() && cudaEventRecord(s->up_done, s->up) != cudaSuccess) {
+      fail_everything(s, "upload event failed");
       return;
     }
-    // bookkeeping and retirement
-    int64_t in_tick = 0;
-    double pi = 0;
+    // finished ticks, then new ticks of every idle batch
     for (auto& kv : s->batches) {
       Batch& b = kv.second;
-      if (b.members.empty()) continue;
-      in_tick += (int64_t)b.members.size();
-      pi += 4.0 * (double)b.pairs_per_rhs;
-      b.bad_host.assign(b.members.size(), 0);
-      cudaError_t ce0 = cudaMemcpy(b.bad_host.data(), b.bad.p, b.members.size() * sizeof(int),
-                                   cudaMemcpyDeviceToHost);
-      if (ce0 != cudaSuccess) {
-        fail_everything(s, std::string("divergence flags: ") + cudaGetErrorString(ce0));
+      cudaError_t e = cudaSuccess;
+      if (b.in_flight) {
+        const cudaError_t q = cudaEventQuery(b.done);
+        if (q == cudaErrorNotReady) continue;
+        b.in_flight = false;
+        if (--s->in_flight == 0) {
+          std::lock_guard<std::mutex> lk(s->mu);
+          s->busy_ms += ms_between(s->busy_since, Clock::now());
+        }
+        e = q == cudaSuccess ? complete_tick(s, b) : q;
+        progress = true;
+      }
+      if (e == cudaSuccess && !b.in_flight && (!b.members.empty() || !b.incoming.empty())) {
+        e = launch_tick(s, b);
+        progress = true;
+      }
+      if (e != cudaSuccess) {
+        fail_everything(s, std::string("tick: ") + cudaGetErrorString(e));
         return;
       }
-      std::vector<Request*> keep;
-      for (size_t i = 0; i < b.members.size(); ++i) {
-        Request* r = b.members[i];
-        r->steps_done += 1;
-        r->t = r->t + r->dt;  // the device does the same addition
-        if (r->steps_done < r->nsteps && !b.bad_host[i]) {
-          keep.push_back(r);
-          continue;
-        }
-        cudaError_t ce = cudaMemcpy(r->x.data(), r->d_state, r->x.size() * sizeof(double),
-                                    cudaMemcpyDeviceToHost);
-        if (ce == cudaSuccess)
-          ce = cudaMemcpy(r->m.data(), r->d_state + 2 * r->n, r->m.size() * sizeof(double),
-                          cudaMemcpyDeviceToHost);
-        cudaFree(r->d_state);
-        r->d_state = nullptr;
-        int status = MMVM_OK;
-        std::string msg;
-        if (ce != cudaSuccess) {
-          status = MMVM_E_DEVICE;
-          msg = std::string("result copy: ") + cudaGetErrorString(ce);
-        } else {
-          for (double v : r->x)
-            if (!std::isfinite(v)) status = MMVM_E_NUMERIC;
-          for (double v : r->m)
-            if (!std::isfinite(v)) status = MMVM_E_NUMERIC;
-          if (status != MMVM_OK) msg = "non-finite value in the state";
-        }
-        std::lock_guard<std::mutex> lk(s->mu);
-        finish_request(s, r, status, msg);
-      }
-      if (keep.size() != b.members.size()) {
-        b.members.swap(keep);
-        b.dirty = true;
-      }
-    }
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->ticks += 1;
-      s->pair_interactions += pi;
-      s->busy_ms += ms_between(t0, t1);
-      s->max_batch = std::max(s->max_batch, in_tick);
     }
     s->cv.notify_all();
+    if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
 
@@ -692,7 +761,7 @@ int mmvm_server_create(const mmvm_server_config* cfg, mmvm_server** out) {
   if (cfg->precision != MMVM_FP64 && cfg->precision != MMVM_MIXED_FP32)
     return fail(MMVM_E_INVALID_ARG, "unknown precision");
   if (cfg->max_active < 0) return fail(MMVM_E_INVALID_ARG, "max_active must be >= 0");
-  if (cfg->flags != 0) return fail(MMVM_E_INVALID_ARG, "unknown flag bits");
+  if (cfg->flags & ~MMVM_FLAG_NO_FAR_FIELD) return fail(MMVM_E_INVALID_ARG, "unknown flag bits");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return fail(MMVM_E_DEVICE, cudaGetErrorString(e));
@@ -707,14 +776,10 @@ int mmvm_server_create(const mmvm_server_config* cfg, mmvm_server** out) {
   if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess ||
       (e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, cfg->device)) !=
           cudaSuccess ||
-      (e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreate(&s->ev0)) != cudaSuccess ||
-      (e = cudaEventCreate(&s->ev1)) != cudaSuccess) {
-    if (s->st) cudaStreamDestroy(s->st);
-    if (s->fork) cudaEventDestroy(s->fork);
-    if (s->ev0) cudaEventDestroy(s->ev0);
-    if (s->ev1) cudaEventDestroy(s->ev1);
+      (e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->up_done, cudaEventDisableTiming)) != cudaSuccess) {
+    if (s->up) cudaStreamDestroy(s->up);
+    if (s->up_done) cudaEventDestroy(s->up_done);
     delete s;
     return fail(MMVM_E_DEVICE, cudaGetErrorString(e));
   }
@@ -733,18 +798,18 @@ void mmvm_server_destroy(mmvm_server* s) {
   s->cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->cfg.device);
-  cudaStreamSynchronize(s->st);
+  for (auto& kv : s->batches)
+    if (kv.second.st) cudaStreamSynchronize(kv.second.st);
+  cudaStreamSynchronize(s->up);
   for (auto& kv : s->batches) {
     for (Request* r : kv.second.members)
       if (r->d_state) cudaFree(r->d_state);
+    for (Request* r : kv.second.incoming)
+      if (r->d_state) cudaFree(r->d_state);
     kv.second.release();
   }
-  if (s->exec) cudaGraphExecDestroy(s->exec);
-  for (cudaEvent_t ev : s->join) cudaEventDestroy(ev);
-  cudaEventDestroy(s->fork);
-  cudaEventDestroy(s->ev0);
-  cudaEventDestroy(s->ev1);
-  cudaStreamDestroy(s->st);
+  cudaEventDestroy(s->up_done);
+  cudaStreamDestroy(s->up);
   for (auto& kv : s->all) delete kv.second;
   delete s;
 }
@@ -856,6 +921,7 @@ int mmvm_server_stats(mmvm_server* s, mmvm_server_counters* out) {
   out->active = s->n_active;
   out->ticks = s->ticks;
   out->max_batch = s->max_batch;
+  out->max_active = s->max_active;
   out->pair_interactions = s->pair_interactions;
   out->busy_ms = s->busy_ms;
   out->footprint_bytes = s->fp_used;

@@ -8,8 +8,10 @@
 * Served results agree with the context API stepping the same simulation
   (mixed: 1e-5 relative on moments, the trajectory tolerance of the parity
   tests; FP64: 1e-12) and, for a small case, with the FP64 oracle.
-* Admission by footprint: a budget that holds one simulation at a time runs
-  them one after another; a request larger than the whole budget is refused.
+* Admission by footprint: a budget that holds the largest simulation alone
+  never holds them all at once; a request larger than the whole budget is
+  refused.
+* A request whose state diverges stops early with MMVM_E_NUMERIC.
 """
 import math
 import time
@@ -63,6 +65,8 @@ def _requests():
         (1, 10, 1000.0, 1.0, 9, 0.01),
         (600, 2, 120.0, 0.55, 4, 0.02),
         (333, 6, 2500.0, 0.5, 2, 0.01),
+        (64, 4, 900.0, 0.5, 4, 0.01),     # shares a batch with the n = 97, M = 4 one
+        (120, 8, 2000.0, 0.45, 2, 0.005),  # shares a batch with the n = 150, M = 8 one
     ]
     out = []
     for i, (n, order, Re, sigma, steps, dt) in enumerate(spec):
@@ -103,7 +107,8 @@ def test_same_alone_and_in_the_mix(mm):
     alone = _alone(mm, reqs, mm.MMVM_MIXED_FP32)
     mixed, st = _mixed(mm, reqs, mm.MMVM_MIXED_FP32)
     assert st["completed"] == len(reqs) and st["failed"] == 0
-    assert st["max_batch"] >= 3  # they really ran together
+    assert st["max_active"] >= 3  # they really ran together
+    assert st["max_batch"] >= 2  # and shared batches
     for (wl, steps), (xa, ma, ia), (xm, mm_, im) in zip(reqs, alone, mixed):
         assert ia["steps"] == im["steps"] == steps
         assert ia["t"] == im["t"]
@@ -152,7 +157,7 @@ def test_admission_by_footprint(mm):
         st = srv.stats()
     assert st["completed"] == len(reqs)
     assert st["peak_footprint_bytes"] <= budget
-    assert st["max_batch"] < len(reqs)
+    assert st["max_active"] < len(reqs)
     # same results as without the budget
     alone = _alone(mm, reqs, mm.MMVM_MIXED_FP32)
     for (xa, ma, _), (xb, mb, _) in zip(alone, out):
