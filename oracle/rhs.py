@@ -233,3 +233,48 @@ def rk4(x, mom, t, dt, nsteps, order, lam0, nu, rhs=rhs_regrouped):
         mom = mom + dt / 6.0 * (k1m + 2.0 * k2m + 2.0 * k3m + k4m)
         t = t + dt
     return x, mom, t
+
+
+def self_rhs_rows(mom_row, lam, order, krows):
+    """dM_k of a single particle (eq:moment_evolutionFinish: A(k) alone, no
+    other particle, no centroid motion) for the moment rows ``krows`` only,
+    with the absolute size of what is summed.
+
+    For each k: sum_l M_l sum_{(i,q)} c_k coef_{I/II}(k,l,i,q) W_c[offset]
+    (the (i,q) terms of eq:FinalSingleI/II), with the velocity jet
+    W_c[gamma] = sum_m M_m H_c(m + gamma) (the paper's regrouped form; H_1, H_2
+    are the exact closed forms of Appendix A.1).  Rows are independent, so a
+    sample of them checks a high-order evaluation whose full term list
+    (about M^6 / 50 terms) would not fit in memory.
+
+    Returns (values, abs_sums): abs_sums[r] = sum over the same terms of
+    |c_k coef M_l| * sum_m |M_m H_c(m + offset)|, the scale against which the
+    rounding of any evaluation of that row is measured.
+    """
+    mom_row = np.asarray(mom_row, dtype=np.float64)
+    P = max(3 * order - 1, 0)
+    H1t, H2t = jet_table_at_zero(P, lam)
+    G = _shift_index(order)
+    W = (H1t[G] @ mom_row, H2t[G] @ mom_row)
+    Wabs = (np.abs(H1t[G]) @ np.abs(mom_row), np.abs(H2t[G]) @ np.abs(mom_row))
+    mi = multi_indices(order)
+    vals, sums = [], []
+    for kc in krows:
+        k1, k2 = mi[kc]
+        ck = c_k(k1, k2, lam)
+        tot = 0.0
+        ab = 0.0
+        for lc, (l1, l2) in enumerate(mi):
+            ml = mom_row[lc]
+            if ml == 0.0:
+                continue
+            for comp, terms in ((0, gamma_I_terms(k1, k2, l1, l2, lam)),
+                                (1, gamma_II_terms(k1, k2, l1, l2, lam))):
+                for coef, (o1, o2) in terms:
+                    g = idx(o1, o2)
+                    f = ck * coef * ml
+                    tot += f * W[comp][g]
+                    ab += abs(f) * Wabs[comp][g]
+        vals.append(tot)
+        sums.append(ab)
+    return np.array(vals), np.array(sums)
