@@ -61,7 +61,7 @@ extern "C" {
 /* Largest order of the all-pairs kernels (jets of order 3M).  Single
  * particles (n == 1) accept any order up to MMVM_MAX_ORDER_SINGLE.          */
 #define MMVM_MAX_ORDER_PAIRS 8
-#define MMVM_MAX_ORDER_SINGLE 16
+#define MMVM_MAX_ORDER_SINGLE 64
 
 /* mmvm_config.flags bits.  In MMVM_MIXED_FP32 mode the particles are put in
  * spatial (Morton) order every step and tile pairs whose bounding boxes are
@@ -69,6 +69,11 @@ extern "C" {
  * rounding take the point-vortex jet (far field); this flag turns that off
  * (every pair takes the full jet).  MMVM_FP64 never uses the far field.     */
 #define MMVM_FLAG_NO_FAR_FIELD 1u
+/* Single particle: evaluate the self term by the separable route (the
+ * coefficient sums of eq:FinalSingleI/II taken one index at a time, no
+ * (k, l, beta) table); always used above order 16, this flag forces it at
+ * any order (n must then be 1).                                            */
+#define MMVM_FLAG_SEPARABLE_SELF 2u
 
 typedef struct mmvm_config {
   int32_t order;        /* truncation order M >= 0                            */
@@ -210,6 +215,7 @@ int mmvm_alu_peak(int32_t device, int32_t precision, double* flops_per_s);
  * nsteps.  The result of a request does not depend on the other requests
  * (its work split and spatial order depend on its own state only).  FP32
  * servers use the far field unless flags holds MMVM_FLAG_NO_FAR_FIELD.
+ * Orders up to 16 (a single particle above that: the context API).
  * Submit, poll and stats are thread-safe.
  * ---------------------------------------------------------------------- */
 typedef struct mmvm_server mmvm_server;

@@ -33,8 +33,9 @@ MMVM_E_DEVICE = -7
 MMVM_FP64 = 0
 MMVM_MIXED_FP32 = 1
 MMVM_FLAG_NO_FAR_FIELD = 1
+MMVM_FLAG_SEPARABLE_SELF = 2
 MMVM_MAX_ORDER_PAIRS = 8
-MMVM_MAX_ORDER_SINGLE = 16
+MMVM_MAX_ORDER_SINGLE = 64
 
 _ERRNAMES = {
     MMVM_E_INVALID_ARG: "INVALID_ARG",

@@ -64,7 +64,7 @@ def _units():
                                   [f"-DMMVM_INST_M={m}", f"-DMMVM_INST_PREC={p}",
                                    f"-DMMVM_INST_V={v}", f"-DMMVM_INST_S={sl}"]))
     for src in ("pair_registry.cu", "particle_kernels.cu", "order.cu", "api.cu", "calibrate.cu",
-                "noalloc.cu", "server.cu", "tables.cpp"):
+                "noalloc.cu", "server.cu", "self_high.cu", "tables.cpp"):
         units.append((src, os.path.splitext(src)[0] + ".o", []))
     return units
 

@@ -27,6 +27,9 @@
 
 namespace {
 
+// Highest order whose finish uses the (k, l, beta) coefficient tables.
+constexpr int kMaxOrderTables = 16;
+
 thread_local std::string g_err;
 
 int fail(int code, const std::string& msg) {
@@ -83,6 +86,8 @@ struct mmvm_ctx {
   DevBuf<float> gbox;  // float4 per group of kGroup sorted positions
   DevBuf<unsigned long long> counts;  // cumulative (near, far) pairs of the all-pairs kernel
   bool far = false;    // FP32 and not MMVM_FLAG_NO_FAR_FIELD: sort + far-field tiles
+  bool high = false;   // single particle through the separable self term (self_high.cu)
+  DevBuf<double> sbinom, sg, sscr;  // its factor tables and scratch
   int order_launches = 0;  // kernels launched by one spatial ordering
   DevBuf<double> e_c, psi0;
   mmvm::PairEntry pe;
@@ -220,6 +225,33 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
       c->ev_pending[slot] = true;
     }
     c->launches += 2;
+  }
+  if (c->high) {  // n == 1: separable self term, dx/dt = 0
+    mmvm::SelfHighArgs H;
+    H.M = c->M;
+    H.K = c->K;
+    H.NB = c->NB;
+    H.Min = min_;
+    H.psi0 = c->psi0.p;
+    H.binom = c->sbinom.p;
+    H.g = c->sg.p;
+    H.lam0sq = lam0sq;
+    H.four_nu = four_nu;
+    H.t_dev = c->t_dev();
+    H.dt_dev = dt_dev;
+    H.cs = cs;
+    H.mode = mode;
+    H.out_dx = c->rdx.p;
+    H.out_dM = c->rdm.p;
+    H.y_x = c->x.p;
+    H.y_M = c->m.p;
+    H.ys_x = c->xs.p;
+    H.ys_M = c->ms.p;
+    H.sum_x = c->xsum.p;
+    H.sum_M = c->msum.p;
+    MMVM_CK(mmvm::launch_self_high(H, c->sscr.p, c->st));
+    c->launches += 5;
+    return MMVM_OK;
   }
   mmvm::FinishArgs A;
   A.n = n;
@@ -401,7 +433,8 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
     return fail(MMVM_E_INVALID_ARG, "lambda0 must be positive and finite");
   if (!(cfg->nu >= 0.0) || !std::isfinite(cfg->nu))
     return fail(MMVM_E_INVALID_ARG, "nu must be >= 0 and finite");
-  if (cfg->flags & ~MMVM_FLAG_NO_FAR_FIELD) return fail(MMVM_E_INVALID_ARG, "unknown flag bits");
+  if (cfg->flags & ~(MMVM_FLAG_NO_FAR_FIELD | MMVM_FLAG_SEPARABLE_SELF))
+    return fail(MMVM_E_INVALID_ARG, "unknown flag bits");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -433,7 +466,21 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
   if ((e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(e, "cudaStreamCreate"));
   c->st = c->own;
-  mmvm::FinishTables T = mmvm::build_finish_tables(c->M);
+  // above this order the (k, l, beta) entries are too many: single particles
+  // take the separable path, which needs only psi0 and two small tables
+  c->high = c->M > kMaxOrderTables || (cfg->flags & MMVM_FLAG_SEPARABLE_SELF);
+  mmvm::FinishTables T = mmvm::build_finish_tables(c->M, c->M <= kMaxOrderTables);
+  if (c->high) {
+    mmvm::SeparableTables ST = mmvm::build_separable_tables(c->M);
+    if ((e = c->sbinom.ensure(ST.binom.size())) != cudaSuccess ||
+        (e = c->sg.ensure(ST.g.size())) != cudaSuccess ||
+        (e = c->sscr.ensure(mmvm::self_high_scratch_doubles(c->M))) != cudaSuccess ||
+        (e = cudaMemcpy(c->sbinom.p, ST.binom.data(), ST.binom.size() * sizeof(double),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->sg.p, ST.g.data(), ST.g.size() * sizeof(double),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(cuda_fail(e, "separable tables"));
+  }
   if ((e = c->k_off.ensure(T.k_off.size())) != cudaSuccess ||
       (e = c->e_l.ensure(T.e_l.size())) != cudaSuccess ||
       (e = c->e_b.ensure(T.e_b.size())) != cudaSuccess ||
@@ -468,7 +515,7 @@ void mmvm_destroy(mmvm_ctx* c) {
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
   for (auto* b : {&c->x, &c->m, &c->xs, &c->ms, &c->xsum, &c->msum, &c->rdx, &c->rdm, &c->scal,
-                  &c->partial, &c->e_c, &c->psi0})
+                  &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr})
     b->release();
   c->rec.release();
   c->counts.release();
@@ -504,6 +551,8 @@ static int set_state_common(mmvm_ctx* c, int64_t n, const double* x, const doubl
   if (!std::isfinite(t)) return fail(MMVM_E_INVALID_ARG, "t must be finite");
   if (n > 1 && c->M > MMVM_MAX_ORDER_PAIRS)
     return fail(MMVM_E_UNSUPPORTED, "order above MMVM_MAX_ORDER_PAIRS for n > 1");
+  if (n > 1 && c->high)
+    return fail(MMVM_E_UNSUPPORTED, "the separable self-term path serves one particle only");
   if (c->cfg.lambda0 * c->cfg.lambda0 + 4.0 * c->cfg.nu * t <= 0.0)
     return fail(MMVM_E_INVALID_ARG, "lambda(t)^2 <= 0");
   MMVM_CK(cudaSetDevice(c->cfg.device));
@@ -623,7 +672,8 @@ int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
     }
     c->graph_ok = true;
   }
-  const int per_step = (c->n > 1 ? 12 + (c->far ? c->order_launches : 0) : 4) + 1;
+  const int per_step =
+      (c->n > 1 ? 12 + (c->far ? c->order_launches : 0) : (c->high ? 20 : 4)) + 1;
   for (int64_t s = 0; s < nsteps; ++s) {
     MMVM_CK(cudaGraphLaunch(c->gexec, c->st));
     c->launches += per_step;

@@ -77,6 +77,28 @@ cudaError_t launch_finish_batch(const BatchFinishArgs& B, int grid, cudaStream_t
 cudaError_t launch_advance_batch(BatchInst* inst, const int* n_inst, int max_inst,
                                  cudaStream_t st);
 
+// Single particle, separable evaluation of the self term (self_high.cu).
+struct SelfHighArgs {
+  int M = 0, K = 0, NB = 0;
+  const double* Min = nullptr;    // stage moments (K)
+  const double* psi0 = nullptr;   // jet at the origin, |alpha| <= 3M (tables.h)
+  const double* binom = nullptr;  // (M+1) x (M+1): C(l, q)
+  const double* g = nullptr;      // M+1: g(j) = 4^{-j} / j!
+  double* at = nullptr;           // scratch (set by the launcher)
+  double* Psi = nullptr;
+  double *U1 = nullptr, *U2 = nullptr, *V1 = nullptr, *V2 = nullptr;
+  double lam0sq = 0, four_nu = 0;
+  const double* t_dev = nullptr;
+  const double* dt_dev = nullptr;
+  double cs = 0;
+  int mode = 0;  // 0: RHS to out_*, 1..4: RK4 stage
+  double *out_dx = nullptr, *out_dM = nullptr;
+  double *y_x = nullptr, *y_M = nullptr, *ys_x = nullptr, *ys_M = nullptr;
+  double *sum_x = nullptr, *sum_M = nullptr;
+};
+size_t self_high_scratch_doubles(int M);
+cudaError_t launch_self_high(SelfHighArgs A, double* scratch, cudaStream_t st);  // 5 launches
+
 cudaError_t launch_prep(int precision, int n, int M, const int* perm, const double* x,
                         const double* mom, const double* t_dev, const double* dt_dev, double cs,
                         double lam0sq, double four_nu, void* rec, void* gbox, cudaStream_t st);

@@ -69,7 +69,8 @@ int fail(int code, const std::string& m) {
   return code;
 }
 
-constexpr int kChunkTarget = 1024;  // sources per chunk (items of similar cost)
+constexpr int kMaxOrderServed = 16;  // the batched finish uses the (k, l, beta) tables
+constexpr int kChunkTarget = 1024;   // sources per chunk (items of similar cost)
 constexpr int kMaxChunks = 16;
 constexpr int kStages = 4;
 constexpr int kCountHdr = 4;  // n_slots, n_pair_items, n_finish_items, n_inst
@@ -816,8 +817,8 @@ void mmvm_server_destroy(mmvm_server* s) {
 
 int mmvm_submit(mmvm_server* s, const mmvm_request* q, uint64_t* ticket) {
   if (!s || !q || !ticket) return fail(MMVM_E_INVALID_ARG, "null argument");
-  if (q->order < 0 || q->order > MMVM_MAX_ORDER_SINGLE)
-    return fail(MMVM_E_UNSUPPORTED, "order above MMVM_MAX_ORDER_SINGLE");
+  if (q->order < 0 || q->order > kMaxOrderServed)
+    return fail(MMVM_E_UNSUPPORTED, "order above 16 (the server's finish tables)");
   if (q->n < 1 || q->n > (1 << 20)) return fail(MMVM_E_INVALID_ARG, "n must be 1 .. 2^20");
   if (q->n > 1 && q->order > MMVM_MAX_ORDER_PAIRS)
     return fail(MMVM_E_UNSUPPORTED, "order above MMVM_MAX_ORDER_PAIRS for n > 1");

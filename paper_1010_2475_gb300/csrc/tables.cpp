@@ -32,14 +32,14 @@ long double pow4l(int e) {
 
 }  // namespace
 
-FinishTables build_finish_tables(int M) {
+FinishTables build_finish_tables(int M, bool entries) {
   FinishTables t;
   t.M = M;
   t.K = n_moments(M);
   t.NB = n_beta(M);
   t.NJ = jet_order(M);
   t.k_off.assign(t.K + 1, 0);
-  for (int kn = 0, kcol = 0; kn <= M; ++kn) {
+  for (int kn = 0, kcol = 0; entries && kn <= M; ++kn) {
     for (int k2 = 0; k2 <= kn; ++k2, ++kcol) {
       const int k1 = kn - k2;
       std::map<std::pair<int, int>, long double> acc;  // (l col, beta col) -> coef
@@ -89,6 +89,17 @@ FinishTables build_finish_tables(int M) {
       const long double s = ((p + q) & 1) ? -1.0L : 1.0L;
       t.psi0[tri(n) + a2] = (double)(-inv4pi * s * r / (long double)(p + q));
     }
+  }
+  return t;
+}
+
+SeparableTables build_separable_tables(int M) {
+  SeparableTables t;
+  t.binom.assign((size_t)(M + 1) * (M + 1), 0.0);
+  t.g.assign((size_t)M + 1, 0.0);
+  for (int a = 0; a <= M; ++a) {
+    for (int b = 0; b <= a; ++b) t.binom[(size_t)a * (M + 1) + b] = (double)binoml(a, b);
+    t.g[a] = (double)(pow4l(-a) / factl(a));
   }
   return t;
 }

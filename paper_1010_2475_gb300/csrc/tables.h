@@ -35,6 +35,15 @@ struct FinishTables {
   std::vector<double> psi0;  // psi0 for |alpha| <= NJ, column q(|alpha|) + alpha_2
 };
 
-FinishTables build_finish_tables(int M);
+// entries = false leaves out the (k, l, beta) entries (their number grows
+// like M^6; the separable single-particle path does not use them).
+FinishTables build_finish_tables(int M, bool entries = true);
+
+// Factors of the separable single-particle path (self_high.cu): binom is
+// row-major (M+1) x (M+1), binom[l][q] = C(l, q); g[j] = 4^{-j} / j!, j <= M.
+struct SeparableTables {
+  std::vector<double> binom, g;
+};
+SeparableTables build_separable_tables(int M);
 
 }  // namespace mmvm
