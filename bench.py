@@ -16,13 +16,13 @@ value      pair-interactions/s of the device-timed steps (state resident in HBM,
            timed region).
 e2e        the same metric through the C ABI with host buffers: set_state from
            pinned host memory, one step, get_state to pinned host memory.
-roofline   the all-pairs kernel (~99% of the step) against the FP32 FMA peak
+roofline   the all-pairs kernel (~97% of the step) against the FP32 FMA peak
            measured in the same run (mmvm_alu_peak: a full-occupancy grid of
            independent FMA chains; nominal 152 SMs x 128 lanes x 2 flop x
            2.07 GHz = 80.5 TFLOP/s); the flops of one launch
-           are the pairs it evaluated on each path (counted by the kernel)
-           times that path's flops per pair (flops_per_pair,
-           far_flops_per_pair).
+           are the work it did on each path (counted by the kernel: near
+           pairs, far pairs source by source, tile expansions) times that
+           path's flops (flops_per_pair, far_flops_per_pair, m2p_flops).
 fp64       the plain FP64 form of the same right-hand side on the first 16384
            particles of the workload (one right-hand side, device-timed).
 served     the served stream (independent random-disk solves: n log-uniform in
@@ -122,6 +122,20 @@ def far_flops_per_pair(M: int) -> int:
     if M == 0:
         return 30 + 8 * 2
     return 30 + 8 * (3 * M - 1) + 8 * (M + 1) * 2 * M
+
+
+M2P_ORDER = [8, 10, 12, 14, 15, 17, 18, 19, 21]  # m2p_order(M) of the CUDA code
+
+
+def m2p_flops(M: int) -> int:
+    """Floating-point operations of one tile-expansion evaluation (one target
+    against one far source tile summed about the tile centre):
+    u = 1/w (~30), rho_q up to order 2M + NA - 1 (8 each), Y[nb] += B_j
+    rho_{j+nb} for 1 <= nb <= 2M, j < NA (8 each), fold into Psi and the
+    (hi, lo) flush (~8 per output), NA = M + P + 1 terms."""
+    na = M + M2P_ORDER[M] + 1
+    nb = (2 * M + 1) * (2 * M + 2) // 2 - 1 if M > 0 else 2
+    return 30 + 8 * (2 * M + na - 2) + 8 * 2 * max(M, 1) * na + 8 * nb
 
 
 # ---------------------------------------------------------------- clocks
@@ -484,7 +498,7 @@ def run_ours(args, wl, rank, world, local_rank):
         ctx.step(wl.dt, 1)
     torch.cuda.synchronize(dev)
     mm.mmvm_pair_time(ctx.handle)
-    near0, far0 = mm.mmvm_pair_counts(ctx.handle)
+    work0 = mm.mmvm_pair_work(ctx.handle)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -505,7 +519,7 @@ def run_ours(args, wl, rank, world, local_rank):
             pair_cnt += cnt
     torch.cuda.synchronize(dev)
     launches = ctx.launches - launches0
-    near1, far1 = mm.mmvm_pair_counts(ctx.handle)
+    work1 = mm.mmvm_pair_work(ctx.handle)
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
@@ -580,9 +594,10 @@ def run_ours(args, wl, rank, world, local_rank):
         avg_pair_s = pair_ms / max(pair_cnt, 1) / 1e3
         fpp = flops_per_pair(wl.order)
         ffp = far_flops_per_pair(wl.order)
-        near_l = (near1 - near0) / max(pair_cnt, 1)
-        far_l = (far1 - far0) / max(pair_cnt, 1)
-        flops_launch = near_l * fpp + far_l * ffp
+        fm2p = m2p_flops(wl.order)
+        near_l, far_l, m2p_l, m2p_pairs_l = [(b - a) / max(pair_cnt, 1)
+                                             for a, b in zip(work0, work1)]
+        flops_launch = near_l * fpp + far_l * ffp + m2p_l * fm2p
         achieved = flops_launch / avg_pair_s / 1e12
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -599,7 +614,10 @@ def run_ours(args, wl, rank, world, local_rank):
                              "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                              "traffic": None, "kernel": "pair_kernel (all-pairs jet + contraction)",
                              "flops_per_pair": {"near": fpp, "far": ffp},
-                             "pairs_per_launch": {"near": near_l, "far": far_l},
+                             "flops_per_tile_expansion": fm2p,
+                             "pairs_per_launch": {"near": near_l, "far_source_by_source": far_l,
+                                                  "far_by_tile_expansion": m2p_pairs_l},
+                             "tile_expansions_per_launch": m2p_l,
                              "flops_per_launch": flops_launch,
                              "launch_ms": avg_pair_s * 1e3,
                              "launches_timed": pair_cnt,

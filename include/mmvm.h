@@ -159,10 +159,16 @@ int mmvm_pair_time(mmvm_ctx* ctx, double* ms, int64_t* count);
 int mmvm_pair_config(const mmvm_ctx* ctx, int32_t* out);
 
 /* Cumulative counts of ordered pairs the all-pairs kernel evaluated since the
- * context was created, by path: full jet (near) and point-vortex multipoles
- * (far, MMVM_MIXED_FP32 only).  The self pair and the tuning launches are not
- * counted.  Waits for the context stream.                                   */
+ * context was created, by path: full jet (near) and point-vortex jet (far,
+ * MMVM_MIXED_FP32 only, source by source or through tile expansions).  The
+ * self pair and the tuning launches are not counted.  Waits for the context
+ * stream.                                                                   */
 int mmvm_pair_counts(mmvm_ctx* ctx, int64_t* near_pairs, int64_t* far_pairs);
+
+/* The same work in detail, out[4]: near pairs, far pairs evaluated source by
+ * source, tile expansions evaluated (one per target and far tile summed
+ * about the tile centre), pairs those expansions covered.                   */
+int mmvm_pair_work(mmvm_ctx* ctx, int64_t* out);
 
 /* Right-hand side without any device allocation.  The paper has no
  * counterpart: this is a variant of mmvm_rhs_device for callers that cannot

@@ -53,7 +53,7 @@ EXPORTS = (
     "mmvm_get_state", "mmvm_get_state_device", "mmvm_rhs", "mmvm_rhs_device",
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
     "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_enable_timing",
-    "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_counts", "mmvm_alu_peak",
+    "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_counts", "mmvm_pair_work", "mmvm_alu_peak",
     "mmvm_rhs_noalloc", "mmvm_server_create", "mmvm_server_destroy", "mmvm_submit",
     "mmvm_poll", "mmvm_server_stats", "mmvm_request_footprint",
 )
@@ -153,6 +153,8 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_alu_peak.argtypes = [ctypes.c_int32, ctypes.c_int32,
                                   ctypes.POINTER(ctypes.c_double)]
     lib.mmvm_alu_peak.restype = ctypes.c_int
+    lib.mmvm_pair_work.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.mmvm_pair_work.restype = ctypes.c_int
     lib.mmvm_pair_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64)]
     lib.mmvm_pair_counts.restype = ctypes.c_int
@@ -288,6 +290,14 @@ def mmvm_alu_peak(device: int = 0, precision: int = MMVM_MIXED_FP32) -> float:
     v = ctypes.c_double()
     _check(load_library().mmvm_alu_peak(device, precision, ctypes.byref(v)))
     return v.value
+
+
+def mmvm_pair_work(h):
+    """(near pairs, far pairs source by source, tile expansions evaluated,
+    pairs covered by tile expansions) of the all-pairs kernel so far."""
+    out = (ctypes.c_int64 * 4)()
+    _check(load_library().mmvm_pair_work(h, out))
+    return tuple(int(v) for v in out)
 
 
 def mmvm_pair_counts(h):

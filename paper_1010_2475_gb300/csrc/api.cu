@@ -83,8 +83,10 @@ struct mmvm_ctx {
   DevBuf<double> x, m, xs, ms, xsum, msum, rdx, rdm, scal, partial;
   DevBuf<unsigned char> rec, order_tmp;
   DevBuf<int> flags, k_off, e_l, e_b, perm;
-  DevBuf<float> gbox;  // float4 per group of kGroup sorted positions
-  DevBuf<unsigned long long> counts;  // cumulative (near, far) pairs of the all-pairs kernel
+  DevBuf<float> gbox;  // group records (gdata_len(M) floats per kGroup sorted positions)
+  // cumulative work of the all-pairs kernel: near pairs, far pairs source by
+  // source, tile expansions evaluated, pairs those expansions covered
+  DevBuf<unsigned long long> counts;
   bool far = false;    // FP32 and not MMVM_FLAG_NO_FAR_FIELD: sort + far-field tiles
   bool high = false;   // single particle through the separable self term (self_high.cu)
   DevBuf<double> sbinom, sg, sscr;  // its factor tables and scratch
@@ -126,8 +128,13 @@ int choose_chunks(const mmvm_ctx* c, int64_t n) {
   per_sm = std::max(per_sm, 1);
   const int64_t tiles = (n + c->pe.tpc - 1) / c->pe.tpc;
   const int64_t slots = (int64_t)std::max(dev_sms, 1) * per_sm;
-  // at least ~4 waves of CTAs, chunks no shorter than 4 tiles of sources
-  int64_t ch = (4 * slots + tiles - 1) / tiles;
+  // ~48 waves of CTAs, chunks no shorter than 4 tiles of sources: target
+  // tiles differ a lot in cost (near vs far tiles), and many small CTAs let
+  // the block scheduler even out the SMs (measured at N = 65536, M = 6 with
+  // 256 targets per CTA: 3 chunks 257 ms, 12 chunks 231 ms, 24 chunks 219 ms,
+  // 48 chunks 217 ms per launch)
+  int64_t ch = (48 * slots + tiles - 1) / tiles;
+  if (const char* f = std::getenv("MMVM_CHUNKS")) ch = std::atoi(f);  // measurement override
   const int64_t max_ch = std::max<int64_t>(1, n / (4 * c->S));
   ch = std::min(std::max<int64_t>(ch, 1), max_ch);
   return (int)ch;
@@ -167,7 +174,8 @@ int ensure_buffers(mmvm_ctx* c, int64_t n) {
     MMVM_CK(grow(c->partial, (size_t)std::max(c->chunks, 4) * c->NB * n));
     if (c->far) {
       MMVM_CK(grow(c->perm, (size_t)n));
-      MMVM_CK(grow(c->gbox, (size_t)4 * ((n + mmvm::kGroup - 1) / mmvm::kGroup)));
+      MMVM_CK(grow(c->gbox, (size_t)mmvm::gdata_len(c->M) *
+                                ((n + mmvm::kGroup - 1) / mmvm::kGroup)));
       MMVM_CK(grow(c->order_tmp, mmvm::spatial_order_temp_bytes((int)n)));
       if (realloc) {
         // count the kernels one ordering launches (the sort's are the library's)
@@ -224,7 +232,7 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
       MMVM_CK(cudaEventRecord(c->ev[slot][1], c->st));
       c->ev_pending[slot] = true;
     }
-    c->launches += 2;
+    c->launches += (c->far ? 2 : 1) + c->pe.nslices;
   }
   if (c->high) {  // n == 1: separable self term, dx/dt = 0
     mmvm::SelfHighArgs H;
@@ -487,7 +495,7 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
       (e = c->e_c.ensure(T.e_c.size())) != cudaSuccess ||
       (e = c->psi0.ensure(T.psi0.size())) != cudaSuccess ||
       (e = c->scal.ensure(2)) != cudaSuccess || (e = c->flags.ensure(2)) != cudaSuccess ||
-      (e = c->counts.ensure(2)) != cudaSuccess)
+      (e = c->counts.ensure(4)) != cudaSuccess)
     return bail(cuda_fail(e, "cudaMalloc(tables)"));
   auto up = [&](void* d, const void* h, size_t bytes) {
     return bytes ? cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
@@ -498,7 +506,7 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
       (e = up(c->e_c.p, T.e_c.data(), T.e_c.size() * sizeof(double))) != cudaSuccess ||
       (e = up(c->psi0.p, T.psi0.data(), T.psi0.size() * sizeof(double))) != cudaSuccess ||
       (e = cudaMemset(c->scal.p, 0, 2 * sizeof(double))) != cudaSuccess ||
-      (e = cudaMemset(c->counts.p, 0, 2 * sizeof(unsigned long long))) != cudaSuccess)
+      (e = cudaMemset(c->counts.p, 0, 4 * sizeof(unsigned long long))) != cudaSuccess)
     return bail(cuda_fail(e, "cudaMemcpy(tables)"));
   if (c->pe.nslices && (e = mmvm::pair_prepare(c->pe, c->S)) != cudaSuccess)
     return bail(cuda_fail(e, "pair kernel shared-memory limit"));
@@ -673,7 +681,9 @@ int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
     c->graph_ok = true;
   }
   const int per_step =
-      (c->n > 1 ? 12 + (c->far ? c->order_launches : 0) : (c->high ? 20 : 4)) + 1;
+      (c->n > 1 ? 4 * ((c->far ? 2 : 1) + c->pe.nslices + 1) + (c->far ? c->order_launches : 0)
+                : (c->high ? 20 : 4)) +
+      1;
   for (int64_t s = 0; s < nsteps; ++s) {
     MMVM_CK(cudaGraphLaunch(c->gexec, c->st));
     c->launches += per_step;
@@ -681,14 +691,23 @@ int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
   return MMVM_OK;
 }
 
-int mmvm_pair_counts(mmvm_ctx* c, int64_t* near_pairs, int64_t* far_pairs) {
-  if (!c || !near_pairs || !far_pairs) return fail(MMVM_E_INVALID_ARG, "null argument");
+int mmvm_pair_work(mmvm_ctx* c, int64_t* out) {
+  if (!c || !out) return fail(MMVM_E_INVALID_ARG, "null argument");
   MMVM_CK(cudaSetDevice(c->cfg.device));
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[4] = {0, 0, 0, 0};
   MMVM_CK(cudaMemcpyAsync(h, c->counts.p, sizeof(h), cudaMemcpyDeviceToHost, c->st));
   MMVM_CK(cudaStreamSynchronize(c->st));
-  *near_pairs = (int64_t)h[0];
-  *far_pairs = (int64_t)h[1];
+  for (int i = 0; i < 4; ++i) out[i] = (int64_t)h[i];
+  return MMVM_OK;
+}
+
+int mmvm_pair_counts(mmvm_ctx* c, int64_t* near_pairs, int64_t* far_pairs) {
+  if (!near_pairs || !far_pairs) return fail(MMVM_E_INVALID_ARG, "null argument");
+  int64_t w[4];
+  const int rc = mmvm_pair_work(c, w);
+  if (rc) return rc;
+  *near_pairs = w[0];
+  *far_pairs = w[1] + w[3];
   return MMVM_OK;
 }
 

@@ -94,6 +94,26 @@ __host__ __device__ constexpr float x_far(int M) {
        : M == 5 ? 66.f : M == 6 ? 74.f : M == 7 ? 80.f : 88.f;
 }
 
+// Far source tiles seen from far enough away are summed through one
+// multipole expansion about the tile's centre instead of source by source.
+// With u = 1/w, w = target - centre, delta_s = source - centre and
+// rho_q(w) = (q-1)! u^q, the shift rho_q(w - delta) = sum_k delta^k/k!
+// rho_{q+k}(w) turns the per-source sums sum_n A'_{s,n} rho_{n+nb} into
+// sum_j B_j rho_{j+nb}(w), B_j = sum_s sum_{n+k=j} A'_{s,n} delta_s^k / k!.
+// Truncating k at m2p_order(M) leaves sum_{k>P} C(q+k-1,k) theta^k below
+// 2e-9 for every jet order q <= 3M when the tile radius is at most theta =
+// 0.1 of the distance from the target group's box to the tile centre.
+__host__ __device__ constexpr int m2p_order(int M) {
+  return M <= 0 ? 8 : M == 1 ? 10 : M == 2 ? 12 : M == 3 ? 14 : M == 4 ? 15
+       : M == 5 ? 17 : M == 6 ? 18 : M == 7 ? 19 : 21;
+}
+__host__ __device__ constexpr int m2p_terms(int M) { return M + m2p_order(M) + 1; }
+constexpr float kM2PTheta2 = 0.01f;  // theta^2
+// Per group of kGroup records (FP32 far field): (min z1, max z1, min z2,
+// max z2) of the hi parts, (centre z1, centre z2, radius, 0), then
+// Re/Im B_j for j < m2p_terms(M); padded to whole float4s.
+__host__ __device__ constexpr int gdata_len(int M) { return round_up(8 + 2 * m2p_terms(M), 4); }
+
 // Compile-time loop: f(std::integral_constant<int, i>) for i in [B, E).
 template <int B, int E, typename F>
 __device__ __forceinline__ void static_for(F&& f) {

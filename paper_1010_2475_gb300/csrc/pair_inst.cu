@@ -21,7 +21,7 @@ constexpr int kLO = kSpec.s[MMVM_INST_S].lo;
 constexpr int kHI = kSpec.s[MMVM_INST_S].hi;
 constexpr int kTPC = kSpec.TPC;
 constexpr int kMINB = kSpec.MINB;
-constexpr bool kSYNC = kSpec.SYNC != 0;
+constexpr int kSYNC = kSpec.SYNC;
 static_assert(kTPC % 32 == 0, "targets per CTA must be whole warps");
 #define MMVM_KERNEL pair_kernel<kM, T, kLO, kHI, kTPC, kMINB, kSYNC>
 #define MMVM_BATCH_KERNEL pair_batch_kernel<kM, T, kLO, kHI, kTPC, kMINB, kSYNC>
@@ -39,7 +39,7 @@ cudaError_t launch_batch_fn(const void* rec, const BatchInst* inst, const int4* 
                             double* partial, cudaStream_t st) {
   MMVM_BATCH_KERNEL<<<grid, kTPC, smem_fn(S), st>>>(static_cast<const T*>(rec), inst, items,
                                                     n_items, counter, S,
-                                                    static_cast<const float4*>(gbox), partial);
+                                                    static_cast<const float*>(gbox), partial);
   return cudaGetLastError();
 }
 cudaError_t occ_batch_fn(int S, int* blocks) {
@@ -50,7 +50,7 @@ cudaError_t launch_fn(const void* rec, int n, int chunk_len, int gy, int S, cons
                       double* partial, unsigned long long* counts, cudaStream_t st) {
   dim3 grid((n + kTPC - 1) / kTPC, gy);
   MMVM_KERNEL<<<grid, kTPC, smem_fn(S), st>>>(static_cast<const T*>(rec), n, chunk_len, S,
-                                              static_cast<const float4*>(gbox), partial, counts);
+                                              static_cast<const float*>(gbox), partial, counts);
   return cudaGetLastError();
 }
 cudaError_t occ_fn(int S, int* blocks) {

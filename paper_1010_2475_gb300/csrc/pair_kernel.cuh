@@ -238,9 +238,14 @@ struct PairNear {
 //   Psi[beta] += -Re((-i)^{beta1 + |beta|} Y[|beta|]) / (2 pi).
 // Y is accumulated per target; fold_far adds it into the Psi slice.
 // Only the multipole orders LO <= nb <= HI of the slice are formed (Y[nb - LO]).
-template <int M, typename T, int LO, int HI>
-struct PairFar {
-  static constexpr int NJ = HI + M;
+// The sums above for NA multipole terms: Y[nb] += sum_{n < NA} A_n rho_{n+nb}(b)
+// for LO <= nb <= HI, u = 1/b with b = (b1 + i b2) + (l1 + i l2) (hi and lo
+// parts; u to first order in the lo part).  A single source passes its A'_n
+// (NA = M + 1); a whole far tile passes its expansion B_j about the tile
+// centre (NA = m2p_terms(M), see common.cuh).
+template <int NA, typename T, int LO, int HI>
+struct FarSums {
+  static constexpr int NQ = HI + NA - 1;  // highest rho order
   static constexpr int NY = HI - LO + 1;
 
   __device__ __forceinline__ static void run(T b1, T b2, T l1, T l2, const T* af, T (&yr)[NY],
@@ -252,15 +257,15 @@ struct PairFar {
     const T nr = ur - (ur * tr - ui * ti), ni = ui - (ur * ti + ui * tr);
     ur = nr;
     ui = ni;
-    T ar[M + 1], ai[M + 1];
+    T ar[NA], ai[NA];
 #pragma unroll
-    for (int n = 0; n <= M; ++n) {
+    for (int n = 0; n < NA; ++n) {
       ar[n] = af[2 * n];
       ai[n] = af[2 * n + 1];
     }
-    // rho_q = (q-1)! u^q, one order at a time; Y[nb] += A'_{q-nb} rho_q
+    // rho_q = (q-1)! u^q, one order at a time; Y[nb] += A_{q-nb} rho_q
     T rr = ur, ri = ui;
-    static_for<1, NJ + 1>([&](auto qc) {
+    static_for<1, NQ + 1>([&](auto qc) {
       constexpr int q = decltype(qc)::value;
       if constexpr (q > 1) {
         const T pr = ur * rr - ui * ri;
@@ -268,7 +273,7 @@ struct PairFar {
         rr = T(q - 1) * pr;
         ri = T(q - 1) * pi;
       }
-      static_for<0, M + 1>([&](auto nc) {
+      static_for<0, NA>([&](auto nc) {
         constexpr int n = decltype(nc)::value;
         constexpr int nb = q - n;
         if constexpr (nb >= LO && nb <= HI) {
@@ -279,6 +284,9 @@ struct PairFar {
     });
   }
 };
+
+template <int M, typename T, int LO, int HI>
+struct PairFar : FarSums<M + 1, T, LO, HI> {};
 
 // Psi[beta] += -Re((-i)^{beta1+|beta|} Y[|beta|]) / (2 pi) over the slice's
 // outputs (acc indexed from column B0).

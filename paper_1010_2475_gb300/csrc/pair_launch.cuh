@@ -10,8 +10,8 @@
 // Other variant parameters (chosen per order by the autotuner):
 //   TPC   targets per CTA (a multiple of 32, so each warp is one group);
 //   MINB  CTAs per SM the register budget must allow;
-//   SYNC  a CTA barrier after every source, which keeps the warps of a CTA on
-//         the same stretch of code so they share instruction-cache lines.
+//   SYNC  > 0: a CTA barrier after every SYNC sources, which keeps the warps
+//         of a CTA on nearby code so they share instruction-cache lines.
 // FP32 runs two passes over the chunk's source tiles: first the tiles whose
 // bounding box is beyond x_far(M) of the warp's target group (point-vortex
 // multipoles, PairFar), then the others (full jet, PairNear); the two paths
@@ -93,30 +93,51 @@ __device__ __forceinline__ void far_source(const float* r, float tz1, float tz2,
   PairFar<M, float, LO, HI>::run(b1, b2, l1, l2, r + HDR + K, yr, yi);
 }
 
+// Group record g (see gdata_len in common.cuh).
+template <int M>
+__device__ __forceinline__ const float* group_rec(const float* __restrict__ gdata, int g) {
+  return gdata + (size_t)g * gdata_len(M);
+}
+
 // Does this warp's target group see source group sg only beyond x_far(M)?
 template <int M>
-__device__ __forceinline__ bool tile_is_far(const float4* __restrict__ gbox, int tgroup,
-                                            int sg) {
-  const float4 sb = gbox[sg];
-  const float4 tb = gbox[tgroup];
+__device__ __forceinline__ bool tile_is_far(const float* __restrict__ gdata, int tgroup, int sg) {
+  const float4 sb = *reinterpret_cast<const float4*>(group_rec<M>(gdata, sg));
+  const float4 tb = *reinterpret_cast<const float4*>(group_rec<M>(gdata, tgroup));
   const float dx = fmaxf(0.f, fmaxf(tb.x - sb.y, sb.x - tb.y));
   const float dy = fmaxf(0.f, fmaxf(tb.z - sb.w, sb.z - tb.w));
   return dx * dx + dy * dy >= x_far(M);
 }
 
+// May source group sg be summed through its expansion about its centre for
+// every target of group tgroup (radius <= theta x distance from the target
+// box to the centre)?
+template <int M>
+__device__ __forceinline__ bool tile_takes_m2p(const float* __restrict__ gdata, int tgroup,
+                                               int sg) {
+  const float4 c = *reinterpret_cast<const float4*>(group_rec<M>(gdata, sg) + 4);
+  const float4 tb = *reinterpret_cast<const float4*>(group_rec<M>(gdata, tgroup));
+  const float dx = fmaxf(0.f, fmaxf(tb.x - c.x, c.x - tb.y));
+  const float dy = fmaxf(0.f, fmaxf(tb.z - c.y, c.y - tb.w));
+  return c.z * c.z <= kM2PTheta2 * (dx * dx + dy * dy);
+}
+
 // The work of one CTA: targets tile0 .. tile0 + TPC - 1 (those below n) of
 // one instance against its sources c0 .. c1 - 1.  rec holds the instance's n
-// records (indices are local to it); gbox: per group of kGroup consecutive
-// records, (min z1, max z1, min z2, max z2) of the hi parts, null disables the
-// far-field path (FP64 always).  out: this chunk's block [NB][n] of the
-// partial sums (coalesced FP64 stores); only the slice's columns are written.
-// counts (nullable): cumulative (near, far) pair counts, added by the first
-// slice only.  Called by every thread of the CTA; begins by writing only its
+// records (indices are local to it); gdata: one record per group of kGroup
+// consecutive records (box of the hi parts, centre, radius, expansion about
+// the centre; see gdata_len), null disables the far-field path (FP64
+// always).  A far tile is summed through its expansion when it is far enough
+// for it (tile_takes_m2p), else source by source with the point-vortex jet.
+// out: this chunk's block [NB][n] of the partial sums (coalesced FP64
+// stores); only the slice's columns are written.  counts (nullable):
+// cumulative (near pairs, far pairs source by source, tile expansions
+// evaluated, pairs they cover), added by the first slice only.  Called by every thread of the CTA; begins by writing only its
 // own shared-memory slots and reuses the tile only after a barrier, so a
 // persistent CTA may call it for one item after another.
-template <int M, typename T, int LO, int HI, int TPC, bool SYNC>
+template <int M, typename T, int LO, int HI, int TPC, int SYNC>
 __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n, int tile0, int c0,
-                                               int c1, int S, const float4* __restrict__ gbox,
+                                               int c1, int S, const float* __restrict__ gdata,
                                                double* __restrict__ out,
                                                unsigned long long* __restrict__ counts,
                                                unsigned char* smem_raw) {
@@ -150,8 +171,9 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
   if constexpr (f32) {
     for (int i = threadIdx.x; i < 2 * NBL * TPC; i += blockDim.x) acc_hi[i] = 0.f;
   }
-  const bool use_far = f32 && gbox != nullptr;
-  unsigned n_near = 0, n_far = 0;  // pairs of this thread's target on each path
+  const bool use_far = f32 && gdata != nullptr;
+  // this thread's target: pairs on each path, tile expansions evaluated
+  unsigned n_near = 0, n_far = 0, n_m2p = 0, n_m2p_pairs = 0;
   // this warp's 32 targets form one group; a warp wholly past n does no work
   // (but still takes part in every barrier)
   const int wfirst = tile0 + warp * 32;
@@ -171,7 +193,37 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
 #pragma unroll 1
       for (int t0 = c0; t0 < c1; t0 += S) {
         const int cnt = min(S, c1 - t0);
-        const bool far = warp_valid && tile_is_far<M>(gbox, tgroup, t0 / kGroup);
+        const int sg = t0 / kGroup;
+        const bool far_tile = warp_valid && tile_is_far<M>(gdata, tgroup, sg);
+        const bool m2p = far_tile && tile_takes_m2p<M>(gdata, tgroup, sg);
+        const bool far = far_tile && !m2p;  // source by source
+        if (m2p) {  // the whole tile through its expansion (warp-uniform, no barrier)
+          constexpr int NA = m2p_terms(M);
+          const float* g = group_rec<M>(gdata, sg);
+          const float cx = g[4], cy = g[5];
+          // w = target - centre = (hi - centre) + lo, as an exact (hi, lo) pair
+          const float d1 = tz1 - cx, d2 = tz2 - cy;
+          const float b1 = d1 + tl1, b2 = d2 + tl2;
+          const float v1 = b1 - d1, v2 = b2 - d2;
+          const float l1 = (d1 - (b1 - v1)) + (tl1 - v1);
+          const float l2 = (d2 - (b2 - v2)) + (tl2 - v2);
+          float yr[NY], yi[NY];
+#pragma unroll
+          for (int b = 0; b < NY; ++b) {
+            yr[b] = 0.f;
+            yi[b] = 0.f;
+          }
+          FarSums<NA, float, LO, HI>::run(b1, b2, l1, l2, g + 8, yr, yi);
+          float tmp[NBL];
+#pragma unroll
+          for (int b = 0; b < NBL; ++b) tmp[b] = 0.f;
+          fold_far<M, float, LO, HI>(yr, yi, tmp);
+          flush_sums<NBL, TPC>(tmp, acc_hi, acc_lo, slot);
+          if (j < n) {
+            n_m2p += 1;
+            n_m2p_pairs += cnt;
+          }
+        }
         if (far && j < n) n_far += cnt;
         if (__syncthreads_or(far)) {
           load_tile(t0, cnt);
@@ -187,7 +239,9 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
             if (far)
               far_source<M, LO, HI>(reinterpret_cast<const float*>(tile) + s * R, tz1, tz2, tl1,
                                     tl2, yr, yi);
-            if constexpr (SYNC) __syncthreads();
+            if constexpr (SYNC > 0) {
+              if (s % SYNC == SYNC - 1 || s == cnt - 1) __syncthreads();  // CTA-uniform
+            }
           }
           if (far) {
             float tmp[NBL];
@@ -206,7 +260,7 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
     const int cnt = min(S, c1 - t0);
     bool near = warp_valid;
     if constexpr (f32) {
-      if (use_far && warp_valid) near = !tile_is_far<M>(gbox, tgroup, t0 / kGroup);
+      if (use_far && warp_valid) near = !tile_is_far<M>(gdata, tgroup, t0 / kGroup);
     }
     if (near && j < n) n_near += cnt;
     if (__syncthreads_or(near)) {
@@ -215,7 +269,9 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
 #pragma unroll 1
       for (int s = 0; s < cnt; ++s) {
         if (near) near_source<M, T, LO, HI>(tile + s * R, t0 + s, j, tz1, tz2, tl1, tl2, acc);
-        if constexpr (SYNC) __syncthreads();
+        if constexpr (SYNC > 0) {
+              if (s % SYNC == SYNC - 1 || s == cnt - 1) __syncthreads();  // CTA-uniform
+            }
       }
       if constexpr (f32) {
         if (near) flush_sums<NBL, TPC>(acc, acc_hi, acc_lo, slot);
@@ -225,9 +281,13 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
   if (LO == 1 && counts != nullptr) {
     const unsigned wn = __reduce_add_sync(0xffffffffu, n_near);
     const unsigned wf = __reduce_add_sync(0xffffffffu, n_far);
+    const unsigned we = __reduce_add_sync(0xffffffffu, n_m2p);
+    const unsigned wp = __reduce_add_sync(0xffffffffu, n_m2p_pairs);
     if ((threadIdx.x & 31) == 0) {
       if (wn) atomicAdd(counts, (unsigned long long)wn);
       if (wf) atomicAdd(counts + 1, (unsigned long long)wf);
+      if (we) atomicAdd(counts + 2, (unsigned long long)we);
+      if (wp) atomicAdd(counts + 3, (unsigned long long)wp);
     }
   }
   if (j < n) {
@@ -247,16 +307,16 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
 
 // One context: grid (target tiles, source chunks) over n records.
 // Layout of `partial`: [chunk][beta column][target] FP64.
-template <int M, typename T, int LO, int HI, int TPC, int MINB, bool SYNC>
+template <int M, typename T, int LO, int HI, int TPC, int MINB, int SYNC>
 __global__ void __launch_bounds__(TPC, MINB)
     pair_kernel(const T* __restrict__ rec, int n, int chunk_len, int S,
-                const float4* __restrict__ gbox, double* __restrict__ partial,
+                const float* __restrict__ gdata, double* __restrict__ partial,
                 unsigned long long* __restrict__ counts) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NB = n_beta(M);
   const int c0 = blockIdx.y * chunk_len;
   const int c1 = min(n, c0 + chunk_len);
-  pair_tile_work<M, T, LO, HI, TPC, SYNC>(rec, n, blockIdx.x * TPC, c0, c1, S, gbox,
+  pair_tile_work<M, T, LO, HI, TPC, SYNC>(rec, n, blockIdx.x * TPC, c0, c1, S, gdata,
                                           partial + (size_t)blockIdx.y * NB * n, counts,
                                           smem_raw);
 }
@@ -264,14 +324,14 @@ __global__ void __launch_bounds__(TPC, MINB)
 // Many independent instances of one order in one persistent launch: every
 // CTA takes work items (instance, target tile, source chunk) from a shared
 // counter until none is left.  Items are listed by the host, costliest first.
-// The counter must be zero at launch (the caller clears it).  gbox (null: no
-// far field) holds the group boxes of the whole batch (instances start on
+// The counter must be zero at launch (the caller clears it).  gdata (null: no
+// far field) holds the group records of the whole batch (instances start on
 // group boundaries).
-template <int M, typename T, int LO, int HI, int TPC, int MINB, bool SYNC>
+template <int M, typename T, int LO, int HI, int TPC, int MINB, int SYNC>
 __global__ void __launch_bounds__(TPC, MINB)
     pair_batch_kernel(const T* __restrict__ rec, const BatchInst* __restrict__ inst,
                       const int4* __restrict__ items, const int* __restrict__ n_items,
-                      int* __restrict__ counter, int S, const float4* __restrict__ gbox,
+                      int* __restrict__ counter, int S, const float* __restrict__ gdata,
                       double* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int item_s;
@@ -290,7 +350,8 @@ __global__ void __launch_bounds__(TPC, MINB)
     const int c0 = w.z * ip.chunk_len;
     const int c1 = min(ip.n, c0 + ip.chunk_len);
     pair_tile_work<M, T, LO, HI, TPC, SYNC>(rec + (size_t)ip.slot0 * R, ip.n, w.y, c0, c1, S,
-                                            gbox ? gbox + ip.slot0 / kGroup : nullptr,
+                                            gdata ? group_rec<M>(gdata, ip.slot0 / kGroup)
+                                                  : nullptr,
                                             partial + ip.part_off + (size_t)w.z * NB * ip.n,
                                             nullptr, smem_raw);
   }

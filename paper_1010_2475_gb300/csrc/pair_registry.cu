@@ -6,62 +6,8 @@
 
 namespace mmvm {
 
-SliceEntry pair_slice_m0_p0_v0_s0();
-SliceEntry pair_slice_m0_p1_v0_s0();
-SliceEntry pair_slice_m1_p0_v0_s0();
-SliceEntry pair_slice_m1_p1_v0_s0();
-SliceEntry pair_slice_m2_p0_v0_s0();
-SliceEntry pair_slice_m2_p1_v0_s0();
-SliceEntry pair_slice_m3_p0_v0_s0();
-SliceEntry pair_slice_m3_p1_v0_s0();
-SliceEntry pair_slice_m4_p0_v0_s0();
-SliceEntry pair_slice_m4_p0_v0_s1();
-SliceEntry pair_slice_m4_p1_v0_s0();
-SliceEntry pair_slice_m4_p1_v1_s0();
-SliceEntry pair_slice_m4_p1_v2_s0();
-SliceEntry pair_slice_m4_p1_v2_s1();
-SliceEntry pair_slice_m5_p0_v0_s0();
-SliceEntry pair_slice_m5_p0_v0_s1();
-SliceEntry pair_slice_m5_p1_v0_s0();
-SliceEntry pair_slice_m5_p1_v1_s0();
-SliceEntry pair_slice_m5_p1_v1_s1();
-SliceEntry pair_slice_m5_p1_v2_s0();
-SliceEntry pair_slice_m5_p1_v2_s1();
-SliceEntry pair_slice_m6_p0_v0_s0();
-SliceEntry pair_slice_m6_p0_v0_s1();
-SliceEntry pair_slice_m6_p0_v0_s2();
-SliceEntry pair_slice_m6_p1_v0_s0();
-SliceEntry pair_slice_m6_p1_v1_s0();
-SliceEntry pair_slice_m6_p1_v1_s1();
-SliceEntry pair_slice_m6_p1_v2_s0();
-SliceEntry pair_slice_m6_p1_v2_s1();
-SliceEntry pair_slice_m6_p1_v2_s2();
-SliceEntry pair_slice_m6_p1_v3_s0();
-SliceEntry pair_slice_m6_p1_v3_s1();
-SliceEntry pair_slice_m7_p0_v0_s0();
-SliceEntry pair_slice_m7_p0_v0_s1();
-SliceEntry pair_slice_m7_p0_v0_s2();
-SliceEntry pair_slice_m7_p0_v0_s3();
-SliceEntry pair_slice_m7_p1_v0_s0();
-SliceEntry pair_slice_m7_p1_v0_s1();
-SliceEntry pair_slice_m7_p1_v1_s0();
-SliceEntry pair_slice_m7_p1_v1_s1();
-SliceEntry pair_slice_m7_p1_v1_s2();
-SliceEntry pair_slice_m8_p0_v0_s0();
-SliceEntry pair_slice_m8_p0_v0_s1();
-SliceEntry pair_slice_m8_p0_v0_s2();
-SliceEntry pair_slice_m8_p0_v0_s3();
-SliceEntry pair_slice_m8_p1_v0_s0();
-SliceEntry pair_slice_m8_p1_v0_s1();
-SliceEntry pair_slice_m8_p1_v0_s2();
-SliceEntry pair_slice_m8_p1_v1_s0();
-SliceEntry pair_slice_m8_p1_v1_s1();
-SliceEntry pair_slice_m8_p1_v1_s2();
-SliceEntry pair_slice_m8_p1_v1_s3();
-SliceEntry pair_slice_m8_p1_v2_s0();
-SliceEntry pair_slice_m8_p1_v2_s1();
-SliceEntry pair_slice_m8_p1_v2_s2();
-SliceEntry pair_slice_m8_p1_v2_s3();
+// the slice entry points of every compiled variant, and fill_slices()
+#include "pair_registry_table.inc"
 
 int pair_variant_count(int M, int precision) {
   if (M < 0 || M > 8 || (precision != 0 && precision != 1)) return 0;
@@ -72,37 +18,7 @@ PairEntry pair_entry(int M, int precision, int v) {
   PairEntry e;
   if (v < 0 || v >= pair_variant_count(M, precision)) return e;
   const VariantSpec sp = variant_spec(M, precision, v);
-  switch ((M * 2 + precision) * kMaxVariants + v) {
-    case 0: e.slices[0] = pair_slice_m0_p0_v0_s0(); break;
-    case 4: e.slices[0] = pair_slice_m0_p1_v0_s0(); break;
-    case 8: e.slices[0] = pair_slice_m1_p0_v0_s0(); break;
-    case 12: e.slices[0] = pair_slice_m1_p1_v0_s0(); break;
-    case 16: e.slices[0] = pair_slice_m2_p0_v0_s0(); break;
-    case 20: e.slices[0] = pair_slice_m2_p1_v0_s0(); break;
-    case 24: e.slices[0] = pair_slice_m3_p0_v0_s0(); break;
-    case 28: e.slices[0] = pair_slice_m3_p1_v0_s0(); break;
-    case 32: e.slices[0] = pair_slice_m4_p0_v0_s0(); e.slices[1] = pair_slice_m4_p0_v0_s1(); break;
-    case 36: e.slices[0] = pair_slice_m4_p1_v0_s0(); break;
-    case 37: e.slices[0] = pair_slice_m4_p1_v1_s0(); break;
-    case 38: e.slices[0] = pair_slice_m4_p1_v2_s0(); e.slices[1] = pair_slice_m4_p1_v2_s1(); break;
-    case 40: e.slices[0] = pair_slice_m5_p0_v0_s0(); e.slices[1] = pair_slice_m5_p0_v0_s1(); break;
-    case 44: e.slices[0] = pair_slice_m5_p1_v0_s0(); break;
-    case 45: e.slices[0] = pair_slice_m5_p1_v1_s0(); e.slices[1] = pair_slice_m5_p1_v1_s1(); break;
-    case 46: e.slices[0] = pair_slice_m5_p1_v2_s0(); e.slices[1] = pair_slice_m5_p1_v2_s1(); break;
-    case 48: e.slices[0] = pair_slice_m6_p0_v0_s0(); e.slices[1] = pair_slice_m6_p0_v0_s1(); e.slices[2] = pair_slice_m6_p0_v0_s2(); break;
-    case 52: e.slices[0] = pair_slice_m6_p1_v0_s0(); break;
-    case 53: e.slices[0] = pair_slice_m6_p1_v1_s0(); e.slices[1] = pair_slice_m6_p1_v1_s1(); break;
-    case 54: e.slices[0] = pair_slice_m6_p1_v2_s0(); e.slices[1] = pair_slice_m6_p1_v2_s1(); e.slices[2] = pair_slice_m6_p1_v2_s2(); break;
-    case 55: e.slices[0] = pair_slice_m6_p1_v3_s0(); e.slices[1] = pair_slice_m6_p1_v3_s1(); break;
-    case 56: e.slices[0] = pair_slice_m7_p0_v0_s0(); e.slices[1] = pair_slice_m7_p0_v0_s1(); e.slices[2] = pair_slice_m7_p0_v0_s2(); e.slices[3] = pair_slice_m7_p0_v0_s3(); break;
-    case 60: e.slices[0] = pair_slice_m7_p1_v0_s0(); e.slices[1] = pair_slice_m7_p1_v0_s1(); break;
-    case 61: e.slices[0] = pair_slice_m7_p1_v1_s0(); e.slices[1] = pair_slice_m7_p1_v1_s1(); e.slices[2] = pair_slice_m7_p1_v1_s2(); break;
-    case 64: e.slices[0] = pair_slice_m8_p0_v0_s0(); e.slices[1] = pair_slice_m8_p0_v0_s1(); e.slices[2] = pair_slice_m8_p0_v0_s2(); e.slices[3] = pair_slice_m8_p0_v0_s3(); break;
-    case 68: e.slices[0] = pair_slice_m8_p1_v0_s0(); e.slices[1] = pair_slice_m8_p1_v0_s1(); e.slices[2] = pair_slice_m8_p1_v0_s2(); break;
-    case 69: e.slices[0] = pair_slice_m8_p1_v1_s0(); e.slices[1] = pair_slice_m8_p1_v1_s1(); e.slices[2] = pair_slice_m8_p1_v1_s2(); e.slices[3] = pair_slice_m8_p1_v1_s3(); break;
-    case 70: e.slices[0] = pair_slice_m8_p1_v2_s0(); e.slices[1] = pair_slice_m8_p1_v2_s1(); e.slices[2] = pair_slice_m8_p1_v2_s2(); e.slices[3] = pair_slice_m8_p1_v2_s3(); break;
-    default: return e;
-  }
+  if (!fill_slices((M * 2 + precision) * kMaxVariants + v, e)) return e;
   e.M = M;
   e.precision = precision;
   e.variant = v;

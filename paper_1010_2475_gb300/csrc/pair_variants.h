@@ -1,7 +1,8 @@
 // Compiled variants of the all-pairs kernel per (order M, precision).  A
 // variant is a list of order slices [lo, hi] of the outputs (one kernel each,
 // launched in turn) plus the CTA shape: TPC targets per CTA, MINB CTAs per SM
-// the register budget must allow, SYNC barrier after every source.  The
+// the register budget must allow, SYNC > 0 a CTA barrier after every SYNC
+// sources (keeps the warps on nearby code for the instruction cache).  The
 // autotuner times the variants on the first state of each size and keeps the
 // fastest.  FP32 keeps 2 x (outputs of the slice) x TPC floats of (hi, lo)
 // sums in shared memory, which bounds TPC for wide slices.
@@ -13,7 +14,7 @@ struct SliceSpec {
   int lo, hi;
 };
 
-constexpr int kMaxVariants = 4;
+constexpr int kMaxVariants = 6;
 constexpr int kMaxSlices = 4;
 
 struct VariantSpec {
@@ -24,7 +25,7 @@ struct VariantSpec {
 
 constexpr int n_variants(int M, int prec) {
   if (prec == 0) return 1;
-  return M <= 3 ? 1 : (M == 7 ? 2 : (M == 6 ? 4 : 3));
+  return M <= 3 ? 1 : (M == 7 ? 3 : (M == 6 ? 6 : 4));
 }
 
 constexpr VariantSpec variant_spec(int M, int prec, int v) {
@@ -49,23 +50,29 @@ constexpr VariantSpec variant_spec(int M, int prec, int v) {
     case 4:
       return v == 0 ? VariantSpec{1, {{1, 8}}, 128, 3, 0}
            : v == 1 ? VariantSpec{1, {{1, 8}}, 256, 1, 1}
-                    : VariantSpec{2, {{1, 5}, {6, 8}}, 128, 2, 1};
+           : v == 2 ? VariantSpec{2, {{1, 5}, {6, 8}}, 128, 2, 1}
+                    : VariantSpec{1, {{1, 8}}, 256, 1, 4};
     case 5:
       return v == 0 ? VariantSpec{1, {{1, 10}}, 256, 1, 1}
            : v == 1 ? VariantSpec{2, {{1, 7}, {8, 10}}, 128, 2, 1}
-                    : VariantSpec{2, {{1, 7}, {8, 10}}, 256, 1, 1};
+           : v == 2 ? VariantSpec{2, {{1, 7}, {8, 10}}, 256, 1, 1}
+                    : VariantSpec{1, {{1, 10}}, 256, 1, 4};
     case 6:
       return v == 0 ? VariantSpec{1, {{1, 12}}, 256, 1, 1}
            : v == 1 ? VariantSpec{2, {{1, 8}, {9, 12}}, 128, 2, 1}
            : v == 2 ? VariantSpec{3, {{1, 6}, {7, 9}, {10, 12}}, 128, 2, 1}
-                    : VariantSpec{2, {{1, 8}, {9, 12}}, 256, 1, 1};
+           : v == 3 ? VariantSpec{2, {{1, 8}, {9, 12}}, 256, 1, 1}
+           : v == 4 ? VariantSpec{1, {{1, 12}}, 256, 1, 4}
+                    : VariantSpec{1, {{1, 12}}, 256, 1, 2};
     case 7:
       return v == 0 ? VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 1}
-                    : VariantSpec{3, {{1, 7}, {8, 11}, {12, 14}}, 128, 2, 1};
+           : v == 1 ? VariantSpec{3, {{1, 7}, {8, 11}, {12, 14}}, 128, 2, 1}
+                    : VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 4};
     default:
       return v == 0 ? VariantSpec{3, {{1, 8}, {9, 12}, {13, 16}}, 128, 2, 1}
            : v == 1 ? VariantSpec{4, {{1, 8}, {9, 11}, {12, 14}, {15, 16}}, 128, 2, 1}
-                    : VariantSpec{4, {{1, 8}, {9, 11}, {12, 14}, {15, 16}}, 256, 1, 1};
+           : v == 2 ? VariantSpec{4, {{1, 8}, {9, 11}, {12, 14}, {15, 16}}, 256, 1, 1}
+                    : VariantSpec{3, {{1, 8}, {9, 12}, {13, 16}}, 128, 2, 4};
   }
 }
 

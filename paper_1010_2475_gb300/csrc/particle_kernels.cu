@@ -70,12 +70,14 @@ __device__ __forceinline__ void make_record(T* __restrict__ r, const double* __r
 
 // Sorted position p holds particle perm[p] (perm == null: identity).  Every
 // warp (kGroup consecutive positions) writes the bounding box of its hi-part
-// centres to gbox (if given).
+// centres at the head of its group record in gdata (if given; records of GL
+// floats, see gdata_len).
 template <typename T>
 __global__ void prep_kernel(int n, int M, int K, int R, const int* __restrict__ perm,
                             const double* __restrict__ x, const double* __restrict__ mom,
                             const double* t_dev, const double* dt_dev, double cs, double lam0sq,
-                            double four_nu, T* __restrict__ rec, float4* __restrict__ gbox) {
+                            double four_nu, T* __restrict__ rec, float* __restrict__ gdata,
+                            int GL) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = p < n;
   float lo1 = 3.4e38f, hi1 = -3.4e38f, lo2 = 3.4e38f, hi2 = -3.4e38f;
@@ -89,7 +91,7 @@ __global__ void prep_kernel(int n, int M, int K, int R, const int* __restrict__ 
       lo2 = hi2 = r[1];
     }
   }
-  if (gbox) {
+  if (gdata) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
@@ -97,7 +99,92 @@ __global__ void prep_kernel(int n, int M, int K, int R, const int* __restrict__ 
       lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
       hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
     }
-    if ((threadIdx.x & 31) == 0 && valid) gbox[p / kGroup] = make_float4(lo1, hi1, lo2, hi2);
+    if ((threadIdx.x & 31) == 0 && valid)
+      *reinterpret_cast<float4*>(gdata + (size_t)(p / kGroup) * GL) =
+          make_float4(lo1, hi1, lo2, hi2);
+  }
+}
+
+// Expansion of every group of kGroup FP32 records about its centre (the
+// centre of its hi-part box; see m2p_order in common.cuh): one warp per group,
+// lane s adds its A'_n delta_s^k / k! into B_{n+k}, then a warp sum; the
+// radius is the largest |delta_s|.  Slots past n (or, in a batch, past their
+// instance's n) do not count.
+template <int M>
+__global__ void group_multipole_kernel(int n, const float* __restrict__ rec,
+                                       float* __restrict__ gdata,
+                                       const BatchInst* __restrict__ inst,
+                                       const int* __restrict__ slot_inst,
+                                       const int* __restrict__ n_slots) {
+  constexpr int K = n_moments(M), R = rec_len<float>(M), P = m2p_order(M);
+  constexpr int NA = m2p_terms(M), GL = gdata_len(M), H = Rec<float>::HDR;
+  const int total = n_slots ? *n_slots : n;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * kGroup < total; g += nwarps) {
+    const int p = g * kGroup + lane;
+    bool valid = p < total;
+    if (valid && inst) {
+      const BatchInst& I = inst[slot_inst[g]];
+      valid = p - I.slot0 < I.n;
+    }
+    float* gd = gdata + (size_t)g * GL;
+    const float4 box = *reinterpret_cast<const float4*>(gd);
+    const float cx = 0.5f * (box.x + box.y), cy = 0.5f * (box.z + box.w);
+    float dr = 0.f, di = 0.f, ar[M + 1], ai[M + 1];
+#pragma unroll
+    for (int q = 0; q <= M; ++q) {
+      ar[q] = 0.f;
+      ai[q] = 0.f;
+    }
+    if (valid) {
+      const float* r = rec + (size_t)p * R;
+      dr = (r[0] - cx) + r[2];
+      di = (r[1] - cy) + r[3];
+#pragma unroll
+      for (int q = 0; q <= M; ++q) {
+        ar[q] = r[H + K + 2 * q];
+        ai[q] = r[H + K + 2 * q + 1];
+      }
+    }
+    float br[NA], bi[NA];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      br[j] = 0.f;
+      bi[j] = 0.f;
+    }
+    float er = 1.f, ei = 0.f;  // delta^k / k!
+    static_for<0, P + 1>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if constexpr (k > 0) {
+        const float tr = (er * dr - ei * di) * (1.f / k);
+        ei = (er * di + ei * dr) * (1.f / k);
+        er = tr;
+      }
+      static_for<0, M + 1>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        br[q + k] = fmaf(ar[q], er, fmaf(-ai[q], ei, br[q + k]));
+        bi[q + k] = fmaf(ar[q], ei, fmaf(ai[q], er, bi[q + k]));
+      });
+    });
+    float rad2 = dr * dr + di * di;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rad2 = fmaxf(rad2, __shfl_xor_sync(0xffffffffu, rad2, o));
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        br[j] += __shfl_xor_sync(0xffffffffu, br[j], o);
+        bi[j] += __shfl_xor_sync(0xffffffffu, bi[j], o);
+      }
+    }
+    if (lane == 0) {
+      *reinterpret_cast<float4*>(gd + 4) = make_float4(cx, cy, sqrtf(rad2), 0.f);
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        gd[8 + 2 * j] = br[j];
+        gd[9 + 2 * j] = bi[j];
+      }
+    }
   }
 }
 
@@ -256,14 +343,15 @@ __device__ __forceinline__ const double* inst_stage_m(const BatchInst& I, int K,
 // written (no kernel reads them).  src = 0 reads the step-start state y,
 // src = 1 the stage state ys; the core is taken at t + cs dt of each instance.
 // With perm_local, sorted slot p holds local particle perm_local[p]; with
-// gbox, every warp (one group of kGroup slots: the loop keeps warps aligned
-// to groups and n_slots is a multiple of kGroup) writes its group's box.
+// gdata, every warp (one group of kGroup slots: the loop keeps warps aligned
+// to groups and n_slots is a multiple of kGroup) writes its group's box at
+// the head of the group's record (GL floats).
 template <typename T>
 __global__ void prep_batch_kernel(int M, int K, int R, const BatchInst* __restrict__ inst,
                                   const int* __restrict__ slot_inst,
                                   const int* __restrict__ n_slots, int src, double cs,
                                   const int* __restrict__ perm_local, T* __restrict__ rec,
-                                  float4* __restrict__ gbox) {
+                                  float* __restrict__ gdata, int GL) {
   const int total = *n_slots;
   for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
     const int p = base + threadIdx.x;  // whole warps are in or out of range
@@ -282,7 +370,7 @@ __global__ void prep_batch_kernel(int M, int K, int R, const BatchInst* __restri
         lo2 = hi2 = r[1];
       }
     }
-    if (gbox) {
+    if (gdata) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
@@ -290,7 +378,9 @@ __global__ void prep_batch_kernel(int M, int K, int R, const BatchInst* __restri
         lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
         hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
       }
-      if ((threadIdx.x & 31) == 0) gbox[p / kGroup] = make_float4(lo1, hi1, lo2, hi2);
+      if ((threadIdx.x & 31) == 0)
+        *reinterpret_cast<float4*>(gdata + (size_t)(p / kGroup) * GL) =
+            make_float4(lo1, hi1, lo2, hi2);
     }
   }
 }
@@ -369,14 +459,18 @@ cudaError_t launch_prep_batch(int precision, int M, const BatchInst* inst, const
                               const int* perm_local, void* rec, void* gbox, cudaStream_t st) {
   const int K = n_moments(M);
   const int threads = 128, blocks = std::max(1, std::min((max_slots + threads - 1) / threads, 4096));
-  if (precision == 1)
+  if (precision == 1) {
     prep_batch_kernel<float><<<blocks, threads, 0, st>>>(M, K, rec_len<float>(M), inst, slot_inst,
                                                          n_slots, src, cs, perm_local,
-                                                         (float*)rec, (float4*)gbox);
-  else
-    prep_batch_kernel<double><<<blocks, threads, 0, st>>>(M, K, rec_len<double>(M), inst,
-                                                          slot_inst, n_slots, src, cs, perm_local,
-                                                          (double*)rec, nullptr);
+                                                         (float*)rec, (float*)gbox,
+                                                         gdata_len(M));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !gbox) return e;
+    return launch_group_multipole(M, 0, rec, gbox, inst, slot_inst, n_slots, max_slots, st);
+  }
+  prep_batch_kernel<double><<<blocks, threads, 0, st>>>(M, K, rec_len<double>(M), inst, slot_inst,
+                                                        n_slots, src, cs, perm_local,
+                                                        (double*)rec, nullptr, 0);
   return cudaGetLastError();
 }
 
@@ -402,6 +496,27 @@ cudaError_t launch_advance_batch(BatchInst* inst, const int* n_inst, int max_ins
   return cudaGetLastError();
 }
 
+cudaError_t launch_group_multipole(int M, int n, const void* rec, void* gdata,
+                                   const BatchInst* inst, const int* slot_inst,
+                                   const int* n_slots, int max_slots, cudaStream_t st) {
+  const int groups = (max_slots + kGroup - 1) / kGroup;
+  const int threads = 128, blocks = std::max(1, std::min((groups * 32 + threads - 1) / threads, 4096));
+  const float* r = static_cast<const float*>(rec);
+  float* g = static_cast<float*>(gdata);
+  switch (M) {
+#define MMVM_GM_CASE(m)                                                                  \
+  case m:                                                                                \
+    group_multipole_kernel<m><<<blocks, threads, 0, st>>>(n, r, g, inst, slot_inst, n_slots); \
+    break;
+    MMVM_GM_CASE(0) MMVM_GM_CASE(1) MMVM_GM_CASE(2) MMVM_GM_CASE(3) MMVM_GM_CASE(4)
+    MMVM_GM_CASE(5) MMVM_GM_CASE(6) MMVM_GM_CASE(7) MMVM_GM_CASE(8)
+#undef MMVM_GM_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prep(int precision, int n, int M, const int* perm, const double* x,
                         const double* mom, const double* t_dev, const double* dt_dev, double cs,
                         double lam0sq, double four_nu, void* rec, void* gbox, cudaStream_t st) {
@@ -410,12 +525,14 @@ cudaError_t launch_prep(int precision, int n, int M, const int* perm, const doub
   if (precision == 1) {
     prep_kernel<float><<<blocks, threads, 0, st>>>(n, M, K, rec_len<float>(M), perm, x, mom,
                                                    t_dev, dt_dev, cs, lam0sq, four_nu,
-                                                   (float*)rec, (float4*)gbox);
-  } else {
-    prep_kernel<double><<<blocks, threads, 0, st>>>(n, M, K, rec_len<double>(M), perm, x, mom,
-                                                    t_dev, dt_dev, cs, lam0sq, four_nu,
-                                                    (double*)rec, nullptr);
+                                                   (float*)rec, (float*)gbox, gdata_len(M));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !gbox) return e;
+    return launch_group_multipole(M, n, rec, gbox, nullptr, nullptr, nullptr, n, st);
   }
+  prep_kernel<double><<<blocks, threads, 0, st>>>(n, M, K, rec_len<double>(M), perm, x, mom,
+                                                  t_dev, dt_dev, cs, lam0sq, four_nu,
+                                                  (double*)rec, nullptr, 0);
   return cudaGetLastError();
 }
 

@@ -56,7 +56,7 @@ struct BatchFinishArgs {
 };
 
 // perm_local (nullable): sorted slot -> local particle index (batch order);
-// gbox (nullable): float4 box per group of kGroup slots (FP32 records only).
+// gbox (nullable, FP32 records only): group records as for launch_prep.
 cudaError_t launch_prep_batch(int precision, int M, const BatchInst* inst, const int* slot_inst,
                               const int* n_slots, int max_slots, int src, double cs,
                               const int* perm_local, void* rec, void* gbox, cudaStream_t st);
@@ -99,9 +99,17 @@ struct SelfHighArgs {
 size_t self_high_scratch_doubles(int M);
 cudaError_t launch_self_high(SelfHighArgs A, double* scratch, cudaStream_t st);  // 5 launches
 
+// Records of the n particles (sorted position p holds particle perm[p]).  For
+// FP32 records with gbox non-null also the group records (gdata_len(M)
+// floats per group of kGroup: box, centre, radius, expansion; two launches).
 cudaError_t launch_prep(int precision, int n, int M, const int* perm, const double* x,
                         const double* mom, const double* t_dev, const double* dt_dev, double cs,
                         double lam0sq, double four_nu, void* rec, void* gbox, cudaStream_t st);
+// Centre, radius and expansion of every group (after the boxes are written);
+// in a batch (inst non-null) n_slots and slot_inst give the slots, else n.
+cudaError_t launch_group_multipole(int M, int n, const void* rec, void* gdata,
+                                   const BatchInst* inst, const int* slot_inst,
+                                   const int* n_slots, int max_slots, cudaStream_t st);
 // Spatial order: perm[p] = particle at sorted position p (Morton order of the
 // centres, ties by index).  temp_bytes() sizes the scratch for n particles.
 size_t spatial_order_temp_bytes(int n);

@@ -103,9 +103,11 @@ uint64_t footprint(int M, int precision, int64_t n) {
   const uint64_t part = (uint64_t)chunks_for(n) * NB * n * 8;
   const uint64_t items = (slots / 32 + 1) * (uint64_t)std::max(chunks_for(n), 1) * 16 +
                          (uint64_t)n * 8 + slots / kGroup * 4 + sizeof(BatchInst);
-  // spatial order of FP32 batches: sorted index, keys and values twice,
-  // group boxes, the simulation's box
-  const uint64_t order = precision == MMVM_MIXED_FP32 ? slots * 28 + slots / kGroup * 16 + 32 : 0;
+  // spatial order and far field of FP32 batches: sorted index, keys and
+  // values twice, group records, the simulation's box
+  const uint64_t order = precision == MMVM_MIXED_FP32
+                             ? slots * 28 + slots / kGroup * 4 * mmvm::gdata_len(M) + 32
+                             : 0;
   return state + recs + part + items + order;
 }
 
@@ -167,7 +169,7 @@ struct Batch {
   DBuf<int2> fitems;
   DBuf<int> counts;  // kCountHdr sizes, then the item counters
   DBuf<int> bad;     // per simulation: non-finite state after the tick
-  DBuf<float> gbox;  // far field: float4 per group of kGroup slots
+  DBuf<float> gbox;  // far field: group records (gdata_len(M) floats per kGroup slots)
   DBuf<int> perm, iin, iout;
   DBuf<unsigned long long> kin, kout;
   DBuf<double> ibox;
@@ -288,7 +290,7 @@ cudaError_t ensure_caps(Batch& b, int slots, int ninst, bool* grown) {
       return e;
     if (b.far) {
       const size_t sb = mmvm::batch_order_temp_bytes(cap);
-      if ((e = b.gbox.ensure((size_t)4 * (cap / kGroup), &g)) != cudaSuccess ||
+      if ((e = b.gbox.ensure((size_t)mmvm::gdata_len(b.M) * (cap / kGroup), &g)) != cudaSuccess ||
           (e = b.perm.ensure(cap, &g)) != cudaSuccess ||
           (e = b.iin.ensure(cap, &g)) != cudaSuccess ||
           (e = b.iout.ensure(cap, &g)) != cudaSuccess ||

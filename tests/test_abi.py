@@ -85,7 +85,9 @@ def test_request_footprint_host_only(lib):
         slots = -(-n // 32) * 32
         chunks = 0 if n <= 1 else min(-(-n // 1024), 16)
         items = (slots // 32 + 1) * max(chunks, 1) * 16 + n * 8 + slots // 32 * 4 + 64
-        order = slots * 28 + slots // 32 * 16 + 32 if prec == mm.MMVM_MIXED_FP32 else 0
+        nt = order + [8, 10, 12, 14, 15, 17, 18, 19, 21][min(order, 8)] + 1  # expansion terms
+        gl = -(-(8 + 2 * nt) // 4) * 4  # floats per group record
+        order = slots * 28 + slots // 32 * 4 * gl + 32 if prec == mm.MMVM_MIXED_FP32 else 0
         return 6 * n * (2 + K) * 8 + slots * rec * eb + chunks * NB * n * 8 + items + order
 
     for order, prec, n in [(2, 1, 64), (4, 1, 4096), (8, 1, 8192), (6, 0, 1000), (10, 1, 1),

@@ -209,6 +209,41 @@ def test_far_field_matches_full_jet(mm):
     assert rhs_error(res["far"][1][rows], oM, 6, wl.lam0) <= MIXED_RHS_TOL
 
 
+@pytest.mark.parametrize("order,kind", [(0, "patches"), (1, "disk"), (2, "disk"), (4, "disk"),
+                                        (6, "patches"), (8, "disk")])
+def test_tile_expansions_match_full_jet(mm, order, kind):
+    """Far tiles summed through their expansion about the tile centre (and
+    the rest source by source) against every pair through the full jet
+    (2e-6), and sampled rows against the oracle (the mixed tolerance); the
+    kernel must really have taken both far routes."""
+    if kind == "patches":
+        wl = mmvm_inputs.two_patches(n=8192, order=order, sigma=0.1, seed=500 + order)
+        if order >= 2:
+            rng = np.random.default_rng(order)
+            wl.moments[:, 3:] = rng.normal(size=wl.moments[:, 3:].shape) * 1e-3 \
+                * wl.moments[:, :1] * wl.lam0 ** 2
+    else:
+        wl = mmvm_inputs.random_disk(n=6000, order=order, radius=30.0, sigma=0.5,
+                                     seed=510 + order)
+    res = {}
+    for name, flags in (("far", 0), ("full", mm.MMVM_FLAG_NO_FAR_FIELD)):
+        with mm.Context(order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32, flags=flags) as ctx:
+            ctx.set_state(wl.x, wl.moments, 0.0)
+            res[name] = ctx.rhs()
+            if name == "far":
+                near, far_pp, n_m2p, m2p_pairs = mm.mmvm_pair_work(ctx.handle)
+    assert n_m2p > 0 and m2p_pairs > 0 and far_pp > 0 and near > 0
+    assert near + far_pp + m2p_pairs == wl.n * (wl.n - 1) + wl.n  # every ordered pair, self included
+    assert vel_error(res["far"][0], res["full"][0]) <= 2e-6
+    if order >= 2:
+        assert rhs_error(res["far"][1], res["full"][1], order, wl.lam0) <= 2e-6
+    rows = np.random.default_rng(5).choice(wl.n, 3, replace=False)
+    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu, rows=rows)
+    assert vel_error(res["far"][0][rows], ox) <= MIXED_RHS_TOL
+    if order >= 2:
+        assert rhs_error(res["far"][1][rows], oM, order, wl.lam0) <= MIXED_RHS_TOL
+
+
 @pytest.mark.parametrize("order", [4, 6, 8])
 def test_every_kernel_variant(mm, order, monkeypatch):
     """Each compiled all-pairs variant reproduces the oracle (mixed precision)."""
