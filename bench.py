@@ -41,8 +41,9 @@ single_m60 one particle at order 60 (1891 moments), Lamb-Oseen core plus a
            (six contexts on their own streams); RHS evaluations/s, the
            multiply-adds of the separable passes against the measured FP64
            peak, and sampled rows against the oracle at t = 0.
-cpu_baseline / --impl reference: the FP64 numpy oracle on sampled target rows
-           against all sources, on the host cores.
+cpu_baseline the FP64 numpy oracle on sampled target rows against all sources,
+           one host core; cpu_baseline_all_cores and --impl reference: one
+           single-threaded oracle process per host core, each on its own rows.
 N > 1 GPUs (torchrun): independent replicas of the workload, one per GPU.
 """
 from __future__ import annotations
@@ -204,6 +205,36 @@ def oracle_rate(wl, rows: int, seed: int = 0):
     return rows * wl.n / dt, dt, sel, ox, oM
 
 
+def _oracle_rows_child(args):
+    """One process of the all-cores oracle timing: its own sample of rows."""
+    n, rows, seed = args
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    from oracle.rhs import rhs_regrouped
+
+    wl = workload(n)
+    rng = np.random.default_rng(seed)
+    # untimed: the oracle's first call builds its coefficient caches
+    rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=rng.choice(wl.n, 1))
+    sel = rng.choice(wl.n, rows, replace=False)
+    t0 = time.perf_counter()
+    rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=sel)
+    return time.perf_counter() - t0
+
+
+def oracle_rate_all_cores(wl, rows_per_proc: int, procs: int, seed: int = 0):
+    """The oracle as it stands, one single-threaded process per host core, each
+    on its own sampled target rows against all sources (rows are
+    independent): pair-interactions/s = all rows x n / the slowest process's
+    compute time.  A spawn pool, so no process inherits a CUDA context."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        secs = pool.map(_oracle_rows_child,
+                        [(wl.n, rows_per_proc, seed + 7919 * i) for i in range(procs)])
+    return procs * rows_per_proc * wl.n / max(secs), max(secs)
+
+
 def cpu_cores_used() -> int:
     v = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or "1"
     try:
@@ -214,22 +245,21 @@ def cpu_cores_used() -> int:
 
 def run_reference(args, wl):
     rows = args.oracle_rows
+    procs = args.oracle_procs or os.cpu_count() or 1
     vals, secs = [], []
-    for s in range(args.warmup):
-        oracle_rate(wl, max(1, rows // 4), seed=1000 + s)
     for s in range(args.steps):
-        v, dt, *_ = oracle_rate(wl, rows, seed=s)
+        v, dt = oracle_rate_all_cores(wl, rows, procs, seed=s)
         vals.append(v)
         secs.append(dt)
-    value = len(vals) * rows * wl.n / sum(secs)
-    sample = (f"{rows} random target rows x all {wl.n} sources per step, one right-hand "
-              f"side at t=0 (FP64 numpy oracle)")
+    value = len(vals) * procs * rows * wl.n / sum(secs)
+    sample = (f"{procs} processes x {rows} random target rows x all {wl.n} sources per "
+              f"step, one right-hand side at t=0 (FP64 numpy oracle, one thread per process)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(wl, {"oracle_rows_per_step": rows}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -468,6 +498,21 @@ def run_single_high(args, mm):
     }
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it)."""
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, pairs_per_step: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput of `world` independent replicas: every rank
+    evaluates the full workload, the job takes the slowest rank's time."""
+    return world * pairs_per_step * steps / (max_ms / 1e3)
+
+
 def run_ours(args, wl, rank, world, local_rank):
     import torch
 
@@ -522,11 +567,9 @@ def run_ours(args, wl, rank, world, local_rank):
     work1 = mm.mmvm_pair_work(ctx.handle)
     total_ms = sum(step_ms)
     if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
         dist.barrier()
-    value = world * pairs_step * args.steps / (total_ms / 1e3)
+    value = replica_value(world, pairs_step, args.steps, total_ms)
 
     # end to end through the C ABI with pinned host buffers
     K = wl.K
@@ -636,6 +679,13 @@ def run_ours(args, wl, rank, world, local_rank):
                 "value": rate, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
                 "sample": f"{args.oracle_rows} random target rows x all {wl.n} sources, one "
                           f"right-hand side at t=0 ({secs:.1f} s, FP64 numpy oracle)"}
+            procs = args.oracle_procs or os.cpu_count() or 1
+            if procs > 1:
+                v_all, secs_all = oracle_rate_all_cores(wl, args.oracle_rows, procs, seed=99)
+                line["cpu_baseline_all_cores"] = {
+                    "value": v_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+                    "sample": f"{procs} processes x {args.oracle_rows} random target rows x all "
+                              f"{wl.n} sources, one right-hand side at t=0 ({secs_all:.1f} s)"}
             line["error_vs_oracle"] = {
                 "rows": args.oracle_rows, "t": 0.0,
                 "xdot_rel": vel_error(gx0[sel], ox),
@@ -655,6 +705,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--oracle-rows", type=int, default=2)
+    ap.add_argument("--oracle-procs", type=int, default=0,
+                    help="processes of the all-cores oracle timing (0: one per host core)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24,
