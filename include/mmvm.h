@@ -199,6 +199,24 @@ int mmvm_pair_work(mmvm_ctx* ctx, int64_t* out);
 int mmvm_rhs_noalloc(const mmvm_config* cfg, int64_t n, double t, const double* d_x,
                      const double* d_moments, double* d_dxdt, double* d_dMdt, void* stream);
 
+/* Diagnostics of the context's current state (eq:vorticity_decomposition):
+ * the vorticity omega(p) = sum_j sum_k M^j_k D^k phi_00(p - x^j; lambda(t))
+ * at npts host points pts (npts x 2, row-major) into the host array omega
+ * (npts), FP64 on the device; orders up to 64.  Waits for the context
+ * stream.  Errors: MMVM_E_INVALID_ARG (null pointer, no state), MMVM_E_UNSUPPORTED
+ * (order above 64), MMVM_E_DEVICE.                                           */
+int mmvm_vorticity(mmvm_ctx* ctx, int64_t npts, const double* pts, double* omega);
+
+/* Nonaxisymmetric enstrophy (eq:nonaxi_enstrophy) about the centre (cx, cy):
+ * E = int (omega - <omega>_theta)^2 dx over the disk of radius r_max, with
+ * <omega>_theta the mean over each circle about the centre; quadrature: nr
+ * Gauss-Legendre nodes in r (weight r dr) times ntheta equispaced angles
+ * (the trapezoid rule, spectrally accurate for the periodic integrand).
+ * The vorticity and the per-ring sums run on the device.  1 <= nr <= 4096,
+ * 4 <= ntheta <= 65536.  Errors as mmvm_vorticity.                          */
+int mmvm_nonaxi_enstrophy(mmvm_ctx* ctx, double cx, double cy, double r_max, int32_t nr,
+                          int32_t ntheta, double* E);
+
 /* Measured fused-multiply-add peak of a device, in flop/s (2 flops per FMA):
  * a full-occupancy grid of independent FMA chains, about 50 ms, timed with
  * CUDA events on a stream of its own.  precision selects the FP64 or the

@@ -54,7 +54,7 @@ EXPORTS = (
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
     "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_enable_timing",
     "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_counts", "mmvm_pair_work", "mmvm_alu_peak",
-    "mmvm_rhs_noalloc", "mmvm_server_create", "mmvm_server_destroy", "mmvm_submit",
+    "mmvm_rhs_noalloc", "mmvm_vorticity", "mmvm_nonaxi_enstrophy", "mmvm_server_create", "mmvm_server_destroy", "mmvm_submit",
     "mmvm_poll", "mmvm_server_stats", "mmvm_request_footprint",
 )
 
@@ -147,6 +147,11 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_enable_timing.restype = ctypes.c_int
     lib.mmvm_pair_time.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
     lib.mmvm_pair_time.restype = ctypes.c_int
+    lib.mmvm_vorticity.argtypes = [P, ctypes.c_int64, D, D]
+    lib.mmvm_vorticity.restype = ctypes.c_int
+    lib.mmvm_nonaxi_enstrophy.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int32, ctypes.c_int32, D]
+    lib.mmvm_nonaxi_enstrophy.restype = ctypes.c_int
     lib.mmvm_rhs_noalloc.argtypes = [ctypes.POINTER(mmvm_config), ctypes.c_int64, ctypes.c_double,
                                      P, P, P, P, P]
     lib.mmvm_rhs_noalloc.restype = ctypes.c_int
@@ -274,6 +279,23 @@ def mmvm_pair_time(h):
     return ms.value, cnt.value
 
 
+def mmvm_vorticity(h, pts) -> np.ndarray:
+    """Vorticity of the context's current state at the points pts (n, 2)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    out = np.empty(pts.shape[0])
+    _check(load_library().mmvm_vorticity(h, pts.shape[0], _dptr(pts), _dptr(out)))
+    return out
+
+
+def mmvm_nonaxi_enstrophy(h, cx: float, cy: float, r_max: float, nr: int = 96,
+                          ntheta: int = 128) -> float:
+    """Nonaxisymmetric enstrophy of the current state about (cx, cy)."""
+    v = np.zeros(1)
+    _check(load_library().mmvm_nonaxi_enstrophy(h, float(cx), float(cy), float(r_max), int(nr),
+                                                 int(ntheta), _dptr(v)))
+    return float(v[0])
+
+
 def mmvm_rhs_noalloc(order: int, lambda0: float, nu: float, precision: int, n: int, t: float,
                      d_x: int, d_moments: int, d_dxdt: int, d_dMdt: int,
                      stream: int = 0) -> None:
@@ -332,6 +354,12 @@ class Context:
 
     def rhs(self):
         return mmvm_rhs(self.handle, self.order)
+
+    def vorticity(self, pts):
+        return mmvm_vorticity(self.handle, pts)
+
+    def nonaxi_enstrophy(self, cx=0.0, cy=0.0, r_max=10.0, nr=96, ntheta=128):
+        return mmvm_nonaxi_enstrophy(self.handle, cx, cy, r_max, nr, ntheta)
 
     def step(self, dt, nsteps=1):
         mmvm_step(self.handle, dt, nsteps)

@@ -90,6 +90,7 @@ struct mmvm_ctx {
   bool far = false;    // FP32 and not MMVM_FLAG_NO_FAR_FIELD: sort + far-field tiles
   bool high = false;   // single particle through the separable self term (self_high.cu)
   DevBuf<double> sbinom, sg, sscr;  // its factor tables and scratch
+  DevBuf<double> dpts, dval, dring;  // diagnostics: points, values, ring sums
   int order_launches = 0;  // kernels launched by one spatial ordering
   DevBuf<double> e_c, psi0;
   mmvm::PairEntry pe;
@@ -523,7 +524,7 @@ void mmvm_destroy(mmvm_ctx* c) {
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
   for (auto* b : {&c->x, &c->m, &c->xs, &c->ms, &c->xsum, &c->msum, &c->rdx, &c->rdm, &c->scal,
-                  &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr})
+                  &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr, &c->dpts, &c->dval, &c->dring})
     b->release();
   c->rec.release();
   c->counts.release();
@@ -688,6 +689,74 @@ int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
     MMVM_CK(cudaGraphLaunch(c->gexec, c->st));
     c->launches += per_step;
   }
+  return MMVM_OK;
+}
+
+int mmvm_vorticity(mmvm_ctx* c, int64_t npts, const double* pts, double* omega) {
+  if (!c || (npts > 0 && (!pts || !omega))) return fail(MMVM_E_INVALID_ARG, "null argument");
+  if (npts < 0 || npts > (int64_t)1 << 28) return fail(MMVM_E_INVALID_ARG, "npts out of range");
+  if (c->n < 1) return fail(MMVM_E_INVALID_ARG, "no state loaded");
+  if (c->M > mmvm::diag_max_order())
+    return fail(MMVM_E_UNSUPPORTED, "order above the diagnostics limit (64)");
+  if (npts == 0) return MMVM_OK;
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  MMVM_CK(c->dpts.ensure(2 * (size_t)npts));
+  MMVM_CK(c->dval.ensure((size_t)npts));
+  MMVM_CK(cudaMemcpyAsync(c->dpts.p, pts, 2 * (size_t)npts * sizeof(double),
+                          cudaMemcpyHostToDevice, c->st));
+  MMVM_CK(mmvm::launch_vorticity((int)c->n, c->M, c->x.p, c->m.p, c->t_dev(),
+                                 c->cfg.lambda0 * c->cfg.lambda0, 4.0 * c->cfg.nu, (int)npts,
+                                 c->dpts.p, c->dval.p, c->st));
+  MMVM_CK(cudaMemcpyAsync(omega, c->dval.p, (size_t)npts * sizeof(double),
+                          cudaMemcpyDeviceToHost, c->st));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  c->launches += 1;
+  return MMVM_OK;
+}
+
+int mmvm_nonaxi_enstrophy(mmvm_ctx* c, double cx, double cy, double r_max, int32_t nr,
+                          int32_t ntheta, double* E) {
+  if (!c || !E) return fail(MMVM_E_INVALID_ARG, "null argument");
+  if (!(r_max > 0.0) || !std::isfinite(r_max) || !std::isfinite(cx) || !std::isfinite(cy) ||
+      nr < 1 || nr > 4096 || ntheta < 4 || ntheta > 65536)
+    return fail(MMVM_E_INVALID_ARG, "bad polar grid");
+  if (c->n < 1) return fail(MMVM_E_INVALID_ARG, "no state loaded");
+  if (c->M > mmvm::diag_max_order())
+    return fail(MMVM_E_UNSUPPORTED, "order above the diagnostics limit (64)");
+  std::vector<double> xg, wg;
+  mmvm::gauss_legendre(nr, xg, wg);
+  const size_t np = (size_t)nr * ntheta;
+  std::vector<double> pts(2 * np);
+  const double two_pi = 6.28318530717958647692;
+  for (int i = 0; i < nr; ++i) {
+    const double r = 0.5 * r_max * (xg[i] + 1.0);
+    for (int l = 0; l < ntheta; ++l) {
+      const double th = two_pi * l / ntheta;
+      pts[2 * ((size_t)i * ntheta + l)] = cx + r * std::cos(th);
+      pts[2 * ((size_t)i * ntheta + l) + 1] = cy + r * std::sin(th);
+    }
+  }
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  MMVM_CK(c->dpts.ensure(2 * np));
+  MMVM_CK(c->dval.ensure(np));
+  MMVM_CK(c->dring.ensure((size_t)nr));
+  MMVM_CK(cudaMemcpyAsync(c->dpts.p, pts.data(), 2 * np * sizeof(double), cudaMemcpyHostToDevice,
+                          c->st));
+  MMVM_CK(mmvm::launch_vorticity((int)c->n, c->M, c->x.p, c->m.p, c->t_dev(),
+                                 c->cfg.lambda0 * c->cfg.lambda0, 4.0 * c->cfg.nu, (int)np,
+                                 c->dpts.p, c->dval.p, c->st));
+  MMVM_CK(mmvm::launch_ring_deviation(nr, ntheta, c->dval.p, c->dring.p, c->st));
+  std::vector<double> ring(nr);
+  MMVM_CK(cudaMemcpyAsync(ring.data(), c->dring.p, nr * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->st));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  c->launches += 2;
+  double e = 0.0;  // sum over rings of (r dr weight) x (angle sum) x (2 pi / ntheta)
+  for (int i = 0; i < nr; ++i) {
+    const double r = 0.5 * r_max * (xg[i] + 1.0);
+    e += 0.5 * r_max * wg[i] * r * ring[i];
+  }
+  *E = e * two_pi / ntheta;
   return MMVM_OK;
 }
 

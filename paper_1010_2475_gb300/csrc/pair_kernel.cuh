@@ -45,9 +45,26 @@ namespace mmvm {
 constexpr double kInvPi = 0.31830988618379067154;
 constexpr double kInv4Pi = 0.07957747154594766788;
 
-template <typename T> __device__ __forceinline__ T rcp(T v);
-template <> __device__ __forceinline__ float rcp<float>(float v) { return __frcp_rn(v); }
-template <> __device__ __forceinline__ double rcp<double>(double v) { return 1.0 / v; }
+// 1/i, correctly rounded (compile-time), for the Kummer series below: the
+// loop index is a run-time value, and a table read is cheaper than a
+// correctly rounded reciprocal at run time.
+struct RecipTable {
+  float f[128];
+  double d[128];
+};
+constexpr RecipTable make_recip_table() {
+  RecipTable t{};
+  for (int i = 1; i < 128; ++i) {
+    t.f[i] = 1.0f / (float)i;
+    t.d[i] = 1.0 / (double)i;
+  }
+  return t;
+}
+static __constant__ RecipTable kRecip = make_recip_table();
+
+template <typename T> __device__ __forceinline__ T recip_of(int i);
+template <> __device__ __forceinline__ float recip_of<float>(int i) { return kRecip.f[i]; }
+template <> __device__ __forceinline__ double recip_of<double>(int i) { return kRecip.d[i]; }
 
 // sum_{k>=0} x^k / ((P+1)(P+2)...(P+k+1)) so that I_P(x) = e^{-x} * sum (x < P).
 template <int P, typename T>
@@ -55,11 +72,12 @@ __device__ __forceinline__ T kummer_sum(T x) {
   constexpr bool f32 = std::is_same<T, float>::value;
   const T eps = f32 ? T(2e-8) : T(5e-18);
   constexpr int kmax = f32 ? 48 : 80;
+  static_assert(P + kmax < 128, "reciprocal table too short");
   T term = T(1.0 / (P + 1));
   T s = term;
 #pragma unroll 1
   for (int k = 1; k < kmax; ++k) {
-    term = term * x * rcp<T>(T(P + 1 + k));
+    term = term * x * recip_of<T>(P + 1 + k);
     s += term;
     if (term <= eps * s) break;
   }

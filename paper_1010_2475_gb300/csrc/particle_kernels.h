@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace mmvm {
@@ -102,6 +104,17 @@ cudaError_t launch_self_high(SelfHighArgs A, double* scratch, cudaStream_t st); 
 // Records of the n particles (sorted position p holds particle perm[p]).  For
 // FP32 records with gbox non-null also the group records (gdata_len(M)
 // floats per group of kGroup: box, centre, radius, expansion; two launches).
+// Diagnostics (diagnostics.cu): omega at npts points (device, interleaved
+// x, y) of the state (x, mom) at the core of time *t_dev; the ring sums of
+// squared deviations from the ring mean of v (nr rings of ntheta values).
+int diag_max_order();
+cudaError_t launch_vorticity(int n, int M, const double* x, const double* mom, const double* t_dev,
+                             double lam0sq, double four_nu, int npts, const double* pts,
+                             double* out, cudaStream_t st);
+cudaError_t launch_ring_deviation(int nr, int ntheta, const double* v, double* ring,
+                                  cudaStream_t st);
+void gauss_legendre(int n, std::vector<double>& xs, std::vector<double>& ws);
+
 cudaError_t launch_prep(int precision, int n, int M, const int* perm, const double* x,
                         const double* mom, const double* t_dev, const double* dt_dev, double cs,
                         double lam0sq, double four_nu, void* rec, void* gbox, cudaStream_t st);
