@@ -498,6 +498,39 @@ def run_single_high(args, mm):
     }
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
+KERNEL_SOURCES = ("common.cuh", "pair_kernel.cuh", "pair_launch.cuh", "pair_variants.h",
+                  "pair_inst.cu")
+
+
+def kernel_source_hash() -> str:
+    """sha256 of the all-pairs kernel's sources (the DRAM traffic recorded by
+    ncu belongs to one version of them)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1010_2475_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(n: int, variant: int, chunks: int):
+    """DRAM bytes per launch from the ncu capture in profiles/, or None when
+    the capture was taken on other kernel sources or another launch shape."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash() or rec.get("n") != n:
+        return None
+    for c in rec.get("captures", []):
+        if c.get("variant") == variant and c.get("chunks") == chunks:
+            return c.get("dram_bytes_per_launch")
+    return None
+
+
 def max_over_ranks(ms: float, dist, device) -> float:
     """The slowest rank's time (every rank gets it)."""
     import torch
@@ -633,6 +666,7 @@ def run_ours(args, wl, rank, world, local_rank):
         c32.close()
 
     line = None
+    pcfg = mm.mmvm_pair_config(ctx.handle)
     if rank == 0:
         avg_pair_s = pair_ms / max(pair_cnt, 1) / 1e3
         fpp = flops_per_pair(wl.order)
@@ -652,10 +686,15 @@ def run_ours(args, wl, rank, world, local_rank):
                         "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state + 8,
                         "steps": args.e2e_steps},
                 "gpu_launches": launches,
-                "pair_kernel_config": mm.mmvm_pair_config(ctx.handle),
+                "pair_kernel_config": pcfg,
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                              "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                             "traffic": None, "kernel": "pair_kernel (all-pairs jet + contraction)",
+                             "traffic": recorded_traffic(wl.n, pcfg["variant"], pcfg["chunks"]),
+                             "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                             "launch (profiles/pair_kernel_traffic.json; null "
+                                             "if the kernel sources or launch shape differ "
+                                             "from the capture)",
+                             "kernel": "pair_kernel (all-pairs jet + contraction)",
                              "flops_per_pair": {"near": fpp, "far": ffp},
                              "flops_per_tile_expansion": fm2p,
                              "pairs_per_launch": {"near": near_l, "far_source_by_source": far_l,
