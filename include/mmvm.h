@@ -199,6 +199,21 @@ int mmvm_pair_work(mmvm_ctx* ctx, int64_t* out);
 int mmvm_rhs_noalloc(const mmvm_config* cfg, int64_t n, double t, const double* d_x,
                      const double* d_moments, double* d_dxdt, double* d_dMdt, void* stream);
 
+/* Adaptive integration of the loaded state from the context's current time
+ * to t_end (>= it) with the Dormand-Prince 5(4) pair (the paper integrates
+ * with an adaptive embedded Runge-Kutta pair at tolerance 1e-8): stage
+ * derivatives through the same RHS as mmvm_rhs, first same as last; a step
+ * is kept when max_i |err_i| / (atol + rtol max(|y_i|, |y5_i|)) <= 1 over
+ * y = (x, M); the next step size is h min(5, max(0.2, 0.9 err^(-1/5))) (at
+ * most h after a rejection); the last step lands on t_end.  h0: the first
+ * step size.  *accepted, *rejected (nullable): the step counts.  Waits for
+ * the context stream after every step (the host decides).  Errors:
+ * MMVM_E_INVALID_ARG, MMVM_E_NUMERIC (non-finite error estimate),
+ * MMVM_E_TIMEOUT (max_steps attempts before t_end; the state is kept at the
+ * last accepted step), MMVM_E_DEVICE.                                        */
+int mmvm_integrate(mmvm_ctx* ctx, double t_end, double h0, double rtol, double atol,
+                   int64_t max_steps, int64_t* accepted, int64_t* rejected);
+
 /* Diagnostics of the context's current state (eq:vorticity_decomposition):
  * the vorticity omega(p) = sum_j sum_k M^j_k D^k phi_00(p - x^j; lambda(t))
  * at npts host points pts (npts x 2, row-major) into the host array omega

@@ -54,7 +54,7 @@ EXPORTS = (
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
     "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_enable_timing",
     "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_counts", "mmvm_pair_work", "mmvm_alu_peak",
-    "mmvm_rhs_noalloc", "mmvm_vorticity", "mmvm_nonaxi_enstrophy", "mmvm_server_create", "mmvm_server_destroy", "mmvm_submit",
+    "mmvm_rhs_noalloc", "mmvm_integrate", "mmvm_vorticity", "mmvm_nonaxi_enstrophy", "mmvm_server_create", "mmvm_server_destroy", "mmvm_submit",
     "mmvm_poll", "mmvm_server_stats", "mmvm_request_footprint",
 )
 
@@ -147,6 +147,10 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_enable_timing.restype = ctypes.c_int
     lib.mmvm_pair_time.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
     lib.mmvm_pair_time.restype = ctypes.c_int
+    lib.mmvm_integrate.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int64,
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.mmvm_integrate.restype = ctypes.c_int
     lib.mmvm_vorticity.argtypes = [P, ctypes.c_int64, D, D]
     lib.mmvm_vorticity.restype = ctypes.c_int
     lib.mmvm_nonaxi_enstrophy.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -279,6 +283,16 @@ def mmvm_pair_time(h):
     return ms.value, cnt.value
 
 
+def mmvm_integrate(h, t_end: float, h0: float = 0.01, rtol: float = 1e-8, atol: float = 1e-8,
+                   max_steps: int = 1000000):
+    """Adaptive Dormand-Prince 5(4) to t_end; returns (accepted, rejected) steps."""
+    a = ctypes.c_int64()
+    r = ctypes.c_int64()
+    _check(load_library().mmvm_integrate(h, float(t_end), float(h0), float(rtol), float(atol),
+                                         int(max_steps), ctypes.byref(a), ctypes.byref(r)))
+    return a.value, r.value
+
+
 def mmvm_vorticity(h, pts) -> np.ndarray:
     """Vorticity of the context's current state at the points pts (n, 2)."""
     pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
@@ -354,6 +368,9 @@ class Context:
 
     def rhs(self):
         return mmvm_rhs(self.handle, self.order)
+
+    def integrate(self, t_end, h0=0.01, rtol=1e-8, atol=1e-8, max_steps=1000000):
+        return mmvm_integrate(self.handle, t_end, h0, rtol, atol, max_steps)
 
     def vorticity(self, pts):
         return mmvm_vorticity(self.handle, pts)

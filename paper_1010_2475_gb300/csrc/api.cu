@@ -91,6 +91,8 @@ struct mmvm_ctx {
   bool high = false;   // single particle through the separable self term (self_high.cu)
   DevBuf<double> sbinom, sg, sscr;  // its factor tables and scratch
   DevBuf<double> dpts, dval, dring;  // diagnostics: points, values, ring sums
+  DevBuf<double> dk;                  // adaptive steps: 7 stage derivatives
+  DevBuf<unsigned long long> derr;    // adaptive steps: error of the step (bits)
   int order_launches = 0;  // kernels launched by one spatial ordering
   DevBuf<double> e_c, psi0;
   mmvm::PairEntry pe;
@@ -209,9 +211,13 @@ int ensure_buffers(mmvm_ctx* c, int64_t n) {
 }
 
 // One RHS evaluation: mode 0 writes (rdx, rdm); modes 1..4 are RK4 stages.
+// out_dx / out_dM (mode 0 only): where the RHS goes (null: the context's own
+// rdx / rdm).
 int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, double cs,
-                const double* dt_dev) {
+                const double* dt_dev, double* out_dx = nullptr, double* out_dM = nullptr) {
   const int n = (int)c->n;
+  if (!out_dx) out_dx = c->rdx.p;
+  if (!out_dM) out_dM = c->rdm.p;
   const double lam0sq = c->cfg.lambda0 * c->cfg.lambda0;
   const double four_nu = 4.0 * c->cfg.nu;
   const int* perm = (n > 1 && c->far) ? c->perm.p : nullptr;
@@ -250,8 +256,8 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
     H.dt_dev = dt_dev;
     H.cs = cs;
     H.mode = mode;
-    H.out_dx = c->rdx.p;
-    H.out_dM = c->rdm.p;
+    H.out_dx = out_dx;
+    H.out_dM = out_dM;
     H.y_x = c->x.p;
     H.y_M = c->m.p;
     H.ys_x = c->xs.p;
@@ -283,8 +289,8 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
   A.dt_dev = dt_dev;
   A.cs = cs;
   A.mode = mode;
-  A.out_dx = c->rdx.p;
-  A.out_dM = c->rdm.p;
+  A.out_dx = out_dx;
+  A.out_dM = out_dM;
   A.y_x = c->x.p;
   A.y_M = c->m.p;
   A.ys_x = c->xs.p;
@@ -524,10 +530,11 @@ void mmvm_destroy(mmvm_ctx* c) {
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
   for (auto* b : {&c->x, &c->m, &c->xs, &c->ms, &c->xsum, &c->msum, &c->rdx, &c->rdm, &c->scal,
-                  &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr, &c->dpts, &c->dval, &c->dring})
+                  &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr, &c->dpts, &c->dval, &c->dring, &c->dk})
     b->release();
   c->rec.release();
   c->counts.release();
+  c->derr.release();
   c->order_tmp.release();
   c->perm.release();
   c->gbox.release();
@@ -689,6 +696,118 @@ int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
     MMVM_CK(cudaGraphLaunch(c->gexec, c->st));
     c->launches += per_step;
   }
+  return MMVM_OK;
+}
+
+int mmvm_integrate(mmvm_ctx* c, double t_end, double h0, double rtol, double atol,
+                   int64_t max_steps, int64_t* accepted, int64_t* rejected) {
+  // Dormand-Prince 5(4): nodes, stage weights, 5th-order weights minus 4th-order
+  static const double kC[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+  static const double kA[7][6] = {
+      {0, 0, 0, 0, 0, 0},
+      {1.0 / 5, 0, 0, 0, 0, 0},
+      {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+      {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+      {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+      {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+      {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+  static const double kB5[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784,
+                                11.0 / 84, 0.0};
+  static const double kB4[7] = {5179.0 / 57600, 0.0, 7571.0 / 16695, 393.0 / 640,
+                                -92097.0 / 339200, 187.0 / 2100, 1.0 / 40};
+  if (!c) return fail(MMVM_E_INVALID_ARG, "null context");
+  if (c->n < 1) return fail(MMVM_E_INVALID_ARG, "no state loaded");
+  if (!std::isfinite(t_end) || !(h0 > 0.0) || !std::isfinite(h0) || !(rtol >= 0.0) ||
+      !(atol >= 0.0) || !(rtol + atol > 0.0) || max_steps < 1)
+    return fail(MMVM_E_INVALID_ARG, "bad t_end, h0, tolerances or max_steps");
+  int64_t acc_n = 0, rej_n = 0;
+  if (accepted) *accepted = 0;
+  if (rejected) *rejected = 0;
+  MMVM_CK(cudaSetDevice(c->cfg.device));
+  double t = 0.0;
+  MMVM_CK(cudaMemcpyAsync(&t, c->t_dev(), sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  if (t_end < t) return fail(MMVM_E_INVALID_ARG, "t_end before the current time");
+  if (t_end == t) return MMVM_OK;
+  if (c->cfg.lambda0 * c->cfg.lambda0 + 4.0 * c->cfg.nu * t_end <= 0.0)
+    return fail(MMVM_E_INVALID_ARG, "lambda(t_end)^2 <= 0");
+  const int n = (int)c->n, K = c->K;
+  const size_t L = (size_t)n * (2 + K);
+  MMVM_CK(c->dk.ensure(7 * L));
+  MMVM_CK(c->derr.ensure(1));
+  c->last_dt = NAN;  // dt_dev holds the step size from here on
+  double* dt = c->dt_dev();
+  auto kx = [&](int s) { return c->dk.p + s * L; };
+  auto km = [&](int s) { return c->dk.p + s * L + 2 * (size_t)n; };
+  static thread_local double h_host;
+  double h = h0;
+  h_host = h;
+  MMVM_CK(cudaMemcpyAsync(dt, &h_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  int rc = enqueue_rhs(c, 0, c->x.p, c->m.p, 0.0, dt, kx(0), km(0));  // k1 = f(t, y)
+  if (rc) return rc;
+  while (t < t_end && acc_n + rej_n < max_steps) {
+    const bool last = t + h >= t_end;
+    if (last) h = t_end - t;
+    h_host = h;
+    MMVM_CK(cudaMemcpyAsync(dt, &h_host, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    for (int s = 1; s < 7; ++s) {
+      mmvm::DPCoef co{};
+      for (int j = 0; j < s; ++j) co.w[j] = kA[s][j];
+      co.count = s;
+      double* ox = s == 6 ? c->xsum.p : c->xs.p;  // stage 7 is the 5th-order solution
+      double* om = s == 6 ? c->msum.p : c->ms.p;
+      MMVM_CK(mmvm::launch_dp_combine(n, K, c->x.p, c->m.p, c->dk.p, co, dt, ox, om, c->st));
+      if ((rc = enqueue_rhs(c, 0, ox, om, kC[s], dt, kx(s), km(s)))) return rc;
+      c->launches += 1;
+    }
+    mmvm::DPCoef ec{};
+    for (int j = 0; j < 7; ++j) ec.w[j] = kB5[j] - kB4[j];
+    ec.count = 7;
+    MMVM_CK(mmvm::launch_dp_error(n, K, c->x.p, c->m.p, c->xsum.p, c->msum.p, c->dk.p, ec, dt,
+                                  rtol, atol, c->derr.p, c->st));
+    unsigned long long bits = 0;
+    MMVM_CK(cudaMemcpyAsync(&bits, c->derr.p, sizeof(bits), cudaMemcpyDeviceToHost, c->st));
+    MMVM_CK(cudaStreamSynchronize(c->st));
+    c->launches += 1;
+    double err;
+    std::memcpy(&err, &bits, sizeof(err));
+    if (!std::isfinite(err)) {
+      if (accepted) *accepted = acc_n;
+      if (rejected) *rejected = rej_n;
+      return fail(MMVM_E_NUMERIC, "non-finite error estimate at t = " + std::to_string(t));
+    }
+    const double fac = err > 0.0 ? 0.9 * std::pow(err, -0.2) : 5.0;
+    if (err <= 1.0) {
+      MMVM_CK(cudaMemcpyAsync(c->x.p, c->xsum.p, 2 * (size_t)n * sizeof(double),
+                              cudaMemcpyDeviceToDevice, c->st));
+      MMVM_CK(cudaMemcpyAsync(c->m.p, c->msum.p, (size_t)K * n * sizeof(double),
+                              cudaMemcpyDeviceToDevice, c->st));
+      MMVM_CK(cudaMemcpyAsync(kx(0), kx(6), L * sizeof(double), cudaMemcpyDeviceToDevice,
+                              c->st));  // first same as last
+      if (last) {
+        t = t_end;
+        static thread_local double t_host;
+        t_host = t;
+        MMVM_CK(cudaMemcpyAsync(c->t_dev(), &t_host, sizeof(double), cudaMemcpyHostToDevice,
+                                c->st));
+        MMVM_CK(cudaStreamSynchronize(c->st));
+      } else {
+        t = t + h;  // the device adds the same two doubles
+        MMVM_CK(mmvm::launch_advance_time(c->t_dev(), dt, c->st));
+        c->launches += 1;
+      }
+      ++acc_n;
+      h = h * std::min(5.0, std::max(0.2, fac));
+    } else {
+      ++rej_n;
+      h = h * std::min(1.0, std::max(0.2, fac));
+    }
+  }
+  MMVM_CK(cudaStreamSynchronize(c->st));
+  if (accepted) *accepted = acc_n;
+  if (rejected) *rejected = rej_n;
+  if (t < t_end)
+    return fail(MMVM_E_TIMEOUT, "step limit reached at t = " + std::to_string(t));
   return MMVM_OK;
 }
 

@@ -115,6 +115,21 @@ cudaError_t launch_ring_deviation(int nr, int ntheta, const double* v, double* r
                                   cudaStream_t st);
 void gauss_legendre(int n, std::vector<double>& xs, std::vector<double>& ws);
 
+// Adaptive Dormand-Prince steps (dopri.cu): out = y + h sum_j w_j k_j over
+// the stage derivatives ks ([count][L], L = n (2 + K), x part first), and the
+// max-norm error of a step into err_bits (the bits of a non-negative double).
+struct DPCoef {
+  double w[7];
+  int count;
+};
+cudaError_t launch_dp_combine(int n, int K, const double* y_x, const double* y_M,
+                              const double* ks, const DPCoef& c, const double* h_dev,
+                              double* out_x, double* out_M, cudaStream_t st);
+cudaError_t launch_dp_error(int n, int K, const double* y_x, const double* y_M,
+                            const double* y5_x, const double* y5_M, const double* ks,
+                            const DPCoef& c, const double* h_dev, double rtol, double atol,
+                            unsigned long long* err_bits, cudaStream_t st);
+
 cudaError_t launch_prep(int precision, int n, int M, const int* perm, const double* x,
                         const double* mom, const double* t_dev, const double* dt_dev, double cs,
                         double lam0sq, double four_nu, void* rec, void* gbox, cudaStream_t st);
