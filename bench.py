@@ -97,19 +97,23 @@ def config_dict(wl, extra=None):
 def flops_per_pair(M: int) -> int:
     """Floating-point operations of one near-field pair in the all-pairs kernel.
 
-    K = (M+1)(M+2)/2 source moments, NB = (2M+1)(2M+2)/2 - 1 correlation
-    outputs Psi[beta], NJ = 3M jet orders:
-      contraction   K * NB multiply-adds                     = 2 K NB
-      jet order n   Laplacian chain, projection, seeds,
-                    Cartesian entries                        ~ 5 (n-1) + 4
-      edge terms    I_n, zbar^n, scaling (per order)         ~ 16
-      Hermite fns   two three-term recurrences               ~ 6 (NJ - 1)
-      setup         separation, |b|^2, masks                 ~ 30 (plus 2 exp)
+    K = (M+1)(M+2)/2 source moments, BMAX = 2M correlation orders,
+    NJ = M + BMAX jet orders:
+      edge columns      beta1 in {0, 1}: 2 BMAX K multiply-adds     = 4 BMAX K
+      Laplacian columns (BMAX-1) K + tri(BMAX-1) (M+1) multiply-adds, x 2
+      jet order n       Laplacian chain and projection 4 (n-1),
+                        entries alpha1 <= M+1: 2 min(n+1, M+2), seeds 8
+      edge terms        I_n, zbar^n, scaling (per order)            ~ 16
+      Hermite fns       two three-term recurrences                  ~ 6 (NJ - 1)
+      setup             separation, |b|^2, masks                    ~ 30 (plus 2 exp)
     """
     K = (M + 1) * (M + 2) // 2
-    NB = (2 * M + 1) * (2 * M + 2) // 2 - 1 if M > 0 else 2
-    NJ = 3 * M if M > 0 else 1
-    return 2 * K * NB + 5 * NJ * (NJ - 1) // 2 + 4 * NJ + 16 * NJ + 6 * (NJ - 1) + 30
+    bmax = 2 * M if M > 0 else 1
+    nj = M + bmax
+    edge = 4 * bmax * K
+    lap = 2 * ((bmax - 1) * K + (bmax - 1) * bmax // 2 * (M + 1)) if bmax >= 2 else 0
+    jet = sum(4 * (n - 1) + 2 * min(n + 1, M + 2) + 8 for n in range(1, nj + 1))
+    return edge + lap + jet + 16 * nj + 6 * (nj - 1) + 30
 
 
 def far_flops_per_pair(M: int) -> int:
@@ -132,10 +136,11 @@ def m2p_flops(M: int) -> int:
     """Floating-point operations of one tile-expansion evaluation (one target
     against one far source tile summed about the tile centre):
     u = 1/w (~30), rho_q up to order 2M + NA - 1 (8 each), Y[nb] += B_j
-    rho_{j+nb} for 1 <= nb <= 2M, j < NA (8 each), fold into Psi and the
-    (hi, lo) flush (~8 per output), NA = M + P + 1 terms."""
+    rho_{j+nb} for 1 <= nb <= 2M, j < NA (8 each), fold into the two edge
+    columns per order and the (hi, lo) flush (~8 per output), NA = M + P + 1
+    terms."""
     na = M + M2P_ORDER[M] + 1
-    nb = (2 * M + 1) * (2 * M + 2) // 2 - 1 if M > 0 else 2
+    nb = 2 * (2 * M if M > 0 else 1)
     return 30 + 8 * (2 * M + na - 2) + 8 * 2 * max(M, 1) * na + 8 * nb
 
 

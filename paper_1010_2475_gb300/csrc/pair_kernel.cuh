@@ -9,12 +9,25 @@
 //     Psi[beta] = sum_m a_m D^{m+beta} psi(b),   1 <= |beta| <= BMAX,
 //     W_1[gamma] = -Psi[gamma + e2],  W_2[gamma] = Psi[gamma + e1],
 // in units where c = 2 lambda^2 = 1: b = s / sqrt(c), a_m = M_m c^{-|m|/2}
-// (the finish kernel undoes the scaling).  Per pair this kernel builds the
-// Cartesian jet D^alpha psi(b), 1 <= |alpha| <= NJ = M + BMAX, one order at a
-// time and adds each order into the K x |beta| correlation before the next
-// order is formed, so only one order of the jet is live in registers.
+// (the finish kernel undoes the scaling).
 //
-// Jet of one order n (derivation in the design notes; every step is exact):
+// Only the edge columns beta1 in {0, 1} (two per order) are contracted with
+// the jet.  Since Lap psi = e^{-x}/pi and D_1^2 = Lap - D_2^2,
+//     Psi[beta] = R[beta] - Psi[beta - 2 e1 + 2 e2]   (beta1 >= 2),
+//     R[beta]   = sum_m a_m D^{m + beta - 2 e1} (e^{-x}/pi),
+// and the Gaussian jet is a product of Hermite functions, so R is a separable
+// double sum (over m2, then m1).  The kernel accumulates the edge columns and
+// R in the same column layout as Psi; the finish kernel applies the
+// recursion to the sums over all sources (in FP64).  Per pair this costs
+// 2 x BMAX x K multiply-adds for the edges and K + (M+1) per Laplacian column
+// group instead of K x |beta| for a full contraction.
+//
+// The jet D^alpha psi(b) is built one order at a time (1 <= |alpha| <= NJ =
+// M + BMAX) and each order is added into the edge columns before the next
+// order is formed, so only one order of the jet is live in registers; only
+// the entries alpha1 <= M + 1 are formed.
+//
+// Jet of one order n (every step is exact):
 //  * psi is radial, psi = Psi(|b|^2) with Psi' = (1 - e^{-x})/(4 pi x), so the
 //    holomorphic edge is  d^n psi / dz^n = (1/4pi) (-1)^{n-1} zbar^n I_{n-1}(x),
 //    I_k(x) = int_0^1 t^k e^{-xt} dt (x = |b|^2, z = b1 + i b2);
@@ -97,6 +110,9 @@ struct PairNear {
   static constexpr int B1 = tri(HI + 1) - 1;
   static constexpr int NBL = B1 - B0;
   static constexpr int HN = NJ >= 2 ? NJ - 1 : 1;  // Hermite functions h_0..h_{NJ-2}
+  // orders |gamma| = |beta| - 2 of the Laplacian columns of the slice
+  static constexpr int GLO = LO > 2 ? LO - 2 : 0;
+  static constexpr int GHI = HI - 2;
   static_assert(LO >= 1 && HI <= bmax_of(M) && LO <= HI, "bad order slice");
 
   // Add one source's contribution (moments a[K], separation b in c = 1 units)
@@ -121,6 +137,24 @@ struct PairNear {
     const T eh2 = dexp(-s2) * (T(1) - q2);
     // ... and e^{-x} at the full separation
     const T E = eh1 * (T(1) - T(2) * b1 * l1) * (eh2 * (T(1) - T(2) * b2 * l2));
+    // Hermite functions at b_hi, one order beyond what is used, then the
+    // first-order correction to b = b_hi + b_lo: hx[k] = h_k(b1)/pi, hy[k] = h_k(b2)
+    T hx[HN + 1], hy[HN + 1];
+    hx[0] = eh1 * T(kInvPi);
+    hy[0] = eh2;
+    hx[1] = T(-2) * b1 * hx[0];
+    hy[1] = T(-2) * b2 * hy[0];
+    static_for<1, HN>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      hx[k + 1] = T(-2) * b1 * hx[k] - T(2 * k) * hx[k - 1];
+      hy[k + 1] = T(-2) * b2 * hy[k] - T(2 * k) * hy[k - 1];
+    });
+    static_for<0, HN>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      hx[k] = fma(l1, hx[k + 1], hx[k]);
+      hy[k] = fma(l2, hy[k + 1], hy[k]);
+    });
+
     // w[n-1] = zbar^n I_{n-1}(x), n = 1..NJ
     T wr[NJ], wi[NJ];
     if (x < T(40)) {
@@ -175,24 +209,14 @@ struct PairNear {
         wi[k] = (T(k) * pi - qi) * rx;
       });
     }
-    // Hermite functions at b_hi, one order beyond what is used, then the
-    // first-order correction to b = b_hi + b_lo: hx[k] = h_k(b1)/pi, hy[k] = h_k(b2)
-    T hx[HN + 1], hy[HN + 1];
-    hx[0] = eh1 * T(kInvPi);
-    hy[0] = eh2;
-    hx[1] = T(-2) * b1 * hx[0];
-    hy[1] = T(-2) * b2 * hy[0];
-    static_for<1, HN>([&](auto kc) {
-      constexpr int k = decltype(kc)::value;
-      hx[k + 1] = T(-2) * b1 * hx[k] - T(2 * k) * hx[k - 1];
-      hy[k + 1] = T(-2) * b2 * hy[k] - T(2 * k) * hy[k - 1];
-    });
-    static_for<0, HN>([&](auto kc) {
-      constexpr int k = decltype(kc)::value;
-      hx[k] = fma(l1, hx[k + 1], hx[k]);
-      hy[k] = fma(l2, hy[k + 1], hy[k]);
-    });
-
+    // This pair's edge columns are summed apart from the running sums and
+    // added to them once the last jet order feeding them is done (order k
+    // takes jet orders k .. k + M): the terms of one pair cancel strongly,
+    // and every other column of the order inherits the edges' rounding
+    // through the recursion.
+    T pe[2 * (HI - LO + 1)];
+#pragma unroll
+    for (int i = 0; i < 2 * (HI - LO + 1); ++i) pe[i] = T(0);
     static_for<NLO, NJ + 1>([&](auto nc) {
       constexpr int n = decltype(nc)::value;
       const T f = T(((n - 1) & 1) ? -kInv4Pi : kInv4Pi) * wmask;
@@ -219,30 +243,65 @@ struct PairNear {
       if constexpr ((n & 3) == 1) { c0 = T(-2) * di; c1 = T(2) * dr; }
       if constexpr ((n & 3) == 2) { c0 = T(-2) * dr; c1 = T(-2) * di; }
       if constexpr ((n & 3) == 3) { c0 = T(2) * di;  c1 = T(-2) * dr; }
-      static_for<0, n + 1>([&](auto ac) {
+      // Cartesian entries alpha = (aa, n - aa) for aa <= M + 1: the edge
+      // columns beta1 = aa - m1 in {0, 1} need no others
+      constexpr int AMAX = n < M + 1 ? n : M + 1;
+      static_for<0, AMAX + 1>([&](auto ac) {
         constexpr int aa = decltype(ac)::value;
         constexpr T s = ((aa >> 1) & 1) ? T(-1) : T(1);
         T ca;
         if constexpr (aa < 2) ca = s * ((aa & 1) ? c1 : c0);
         else ca = s * ((aa & 1) ? c1 : c0) + chi[aa];
-        // alpha = (aa, n - aa);  beta = alpha - m for every moment m <= alpha
-        static_for<0, M + 1>([&](auto m1c) {
-          constexpr int m1 = decltype(m1c)::value;
-          static_for<0, M - m1 + 1>([&](auto m2c) {
-            constexpr int m2 = decltype(m2c)::value;
-            constexpr int bb1 = aa - m1;
-            constexpr int bb2 = n - aa - m2;
-            constexpr int bn = bb1 + bb2;
-            if constexpr (bb1 >= 0 && bb2 >= 0 && bn >= 1 && bn <= BMAX) {
-              constexpr int col = bcol(bb1, bb2);
-              if constexpr (col >= B0 && col < B1) {
-                acc[col - B0] += a[mcol(m1, m2)] * ca;
+        static_for<0, 2>([&](auto bc) {
+          constexpr int bb1 = decltype(bc)::value;
+          constexpr int m1 = aa - bb1;
+          if constexpr (m1 >= 0 && m1 <= M) {
+            static_for<0, M - m1 + 1>([&](auto m2c) {
+              constexpr int m2 = decltype(m2c)::value;
+              constexpr int bb2 = n - aa - m2;
+              constexpr int bn = bb1 + bb2;
+              if constexpr (bb2 >= 0 && bn >= LO && bn <= HI) {
+                constexpr int e = 2 * (bn - LO) + bb1;
+                pe[e] = fma(a[mcol(m1, m2)], ca, pe[e]);
               }
-            }
-          });
+            });
+          }
         });
       });
+      constexpr int kd = n - M;  // edge order completed by this jet order
+      if constexpr (kd >= LO && kd <= HI) {
+        acc[bcol(0, kd) - B0] += pe[2 * (kd - LO)];
+        acc[bcol(1, kd - 1) - B0] += pe[2 * (kd - LO) + 1];
+      }
     });
+    // Laplacian columns (beta1 >= 2): R[beta] = sum_m a_m e_(m + beta - 2 e1),
+    // taken one gamma2 = beta2 at a time as sum_m1 hx[m1 + gamma1] T[m1] with
+    // T[m1] = sum_m2 a_(m1, m2) hy[m2 + gamma2] (the Gaussian jet is separable).
+    if constexpr (GHI >= 0) {
+      static_for<0, GHI + 1>([&](auto g2c) {
+        constexpr int g2 = decltype(g2c)::value;
+        T tq[M + 1];
+        static_for<0, M + 1>([&](auto m1c) {
+          constexpr int m1 = decltype(m1c)::value;
+          T sacc = T(0);
+          static_for<0, M - m1 + 1>([&](auto m2c) {
+            constexpr int m2 = decltype(m2c)::value;
+            sacc = fma(a[mcol(m1, m2)], hy[m2 + g2], sacc);
+          });
+          tq[m1] = sacc;
+        });
+        static_for<(GLO > g2 ? GLO - g2 : 0), GHI - g2 + 1>([&](auto g1c) {
+          constexpr int g1 = decltype(g1c)::value;
+          constexpr int col = bcol(g1 + 2, g2) - B0;
+          T sacc = T(0);
+          static_for<0, M + 1>([&](auto m1c) {
+            constexpr int m1 = decltype(m1c)::value;
+            sacc = fma(hx[m1 + g1], tq[m1], sacc);
+          });
+          acc[col] += sacc;  // one rounding against the running sum per pair
+        });
+      });
+    }
   }
 };
 
@@ -306,8 +365,10 @@ struct FarSums {
 template <int M, typename T, int LO, int HI>
 struct PairFar : FarSums<M + 1, T, LO, HI> {};
 
-// Psi[beta] += -Re((-i)^{beta1+|beta|} Y[|beta|]) / (2 pi) over the slice's
-// outputs (acc indexed from column B0).
+// Psi[beta] += -Re((-i)^{beta1+|beta|} Y[|beta|]) / (2 pi) over the edge
+// columns beta1 in {0, 1} of the slice (acc indexed from column B0).  The
+// point-vortex stream function is harmonic, so its Laplacian columns
+// (beta1 >= 2) get nothing: the finish recovers them by the recursion.
 template <int M, typename T, int LO, int HI>
 __device__ __forceinline__ void fold_far(const T (&yr)[HI - LO + 1], const T (&yi)[HI - LO + 1],
                                          T* acc) {
@@ -315,15 +376,17 @@ __device__ __forceinline__ void fold_far(const T (&yr)[HI - LO + 1], const T (&y
   constexpr T s = T(1.0 / (2.0 * 3.14159265358979323846));
   static_for<LO, HI + 1>([&](auto nbc) {
     constexpr int nb = decltype(nbc)::value;
-    static_for<0, nb + 1>([&](auto b2c) {
-      constexpr int bb2 = decltype(b2c)::value;
-      constexpr int bb1 = nb - bb2;
-      constexpr int col = bcol(bb1, bb2) - PN::B0;
-      constexpr int r = (bb1 + nb) & 3;
-      if constexpr (r == 0) acc[col] -= s * yr[nb - LO];
-      if constexpr (r == 1) acc[col] -= s * yi[nb - LO];
-      if constexpr (r == 2) acc[col] += s * yr[nb - LO];
-      if constexpr (r == 3) acc[col] += s * yi[nb - LO];
+    static_for<0, 2>([&](auto b1c) {
+      constexpr int bb1 = decltype(b1c)::value;
+      if constexpr (bb1 <= nb) {
+        constexpr int bb2 = nb - bb1;
+        constexpr int col = bcol(bb1, bb2) - PN::B0;
+        constexpr int r = (bb1 + nb) & 3;
+        if constexpr (r == 0) acc[col] -= s * yr[nb - LO];
+        if constexpr (r == 1) acc[col] -= s * yi[nb - LO];
+        if constexpr (r == 2) acc[col] += s * yr[nb - LO];
+        if constexpr (r == 3) acc[col] += s * yi[nb - LO];
+      }
     });
   });
 }

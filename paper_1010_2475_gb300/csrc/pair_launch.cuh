@@ -61,20 +61,36 @@ __device__ __forceinline__ void near_source(const T* r, int src, int j, T tz1, T
   PN::run(b1, b2, l1, l2, wm, a, accr);
 }
 
+// Fold one FP32 register sum into this thread's shared-memory (hi, lo) pair.
+__device__ __forceinline__ void flush_one(float& v, float* acc_hi, float* acc_lo, int idx) {
+  const float hi = acc_hi[idx];
+  const float sum = hi + v;
+  const float bp = sum - hi;
+  const float err = (hi - (sum - bp)) + (v - bp);
+  acc_hi[idx] = sum;
+  acc_lo[idx] += err;
+  v = 0.f;
+}
+
 // Fold FP32 register sums into this thread's shared-memory (hi, lo) pairs.
 template <int NBL, int TPC>
 __device__ __forceinline__ void flush_sums(float* acc, float* acc_hi, float* acc_lo, int slot) {
 #pragma unroll
-  for (int b = 0; b < NBL; ++b) {
-    const int idx = b * TPC + slot;
-    const float hi = acc_hi[idx];
-    const float sum = hi + acc[b];
-    const float bp = sum - hi;
-    const float err = (hi - (sum - bp)) + (acc[b] - bp);
-    acc_hi[idx] = sum;
-    acc_lo[idx] += err;
-    acc[b] = 0.f;
-  }
+  for (int b = 0; b < NBL; ++b) flush_one(acc[b], acc_hi, acc_lo, b * TPC + slot);
+}
+
+// The same for the edge columns (beta1 in {0, 1}) of a slice only: the far
+// field writes nothing else.
+template <int M, int LO, int HI, int TPC>
+__device__ __forceinline__ void flush_edge_sums(float* acc, float* acc_hi, float* acc_lo,
+                                                int slot) {
+  constexpr int B0 = PairNear<M, float, LO, HI>::B0;
+  static_for<LO, HI + 1>([&](auto nbc) {
+    constexpr int nb = decltype(nbc)::value;
+    constexpr int c0 = bcol(0, nb) - B0, c1 = bcol(1, nb - 1) - B0;
+    flush_one(acc[c0], acc_hi, acc_lo, c0 * TPC + slot);
+    flush_one(acc[c1], acc_hi, acc_lo, c1 * TPC + slot);
+  });
 }
 
 // One far-field source (FP32): multipole sums of the tile in yr/yi.
@@ -218,7 +234,7 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
 #pragma unroll
           for (int b = 0; b < NBL; ++b) tmp[b] = 0.f;
           fold_far<M, float, LO, HI>(yr, yi, tmp);
-          flush_sums<NBL, TPC>(tmp, acc_hi, acc_lo, slot);
+          flush_edge_sums<M, LO, HI, TPC>(tmp, acc_hi, acc_lo, slot);
           if (j < n) {
             n_m2p += 1;
             n_m2p_pairs += cnt;
@@ -248,7 +264,7 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
 #pragma unroll
             for (int b = 0; b < NBL; ++b) tmp[b] = 0.f;
             fold_far<M, float, LO, HI>(yr, yi, tmp);
-            flush_sums<NBL, TPC>(tmp, acc_hi, acc_lo, slot);
+            flush_edge_sums<M, LO, HI, TPC>(tmp, acc_hi, acc_lo, slot);
           }
         }
       }

@@ -14,7 +14,7 @@ struct SliceSpec {
   int lo, hi;
 };
 
-constexpr int kMaxVariants = 6;
+constexpr int kMaxVariants = 8;
 constexpr int kMaxSlices = 4;
 
 struct VariantSpec {
@@ -25,7 +25,7 @@ struct VariantSpec {
 
 constexpr int n_variants(int M, int prec) {
   if (prec == 0) return 1;
-  return M <= 3 ? 1 : (M == 7 ? 3 : (M == 6 ? 6 : 4));
+  return M <= 3 ? 1 : (M == 7 ? 3 : (M == 6 ? 8 : (M == 8 ? 4 : 6)));
 }
 
 constexpr VariantSpec variant_spec(int M, int prec, int v) {
@@ -51,19 +51,25 @@ constexpr VariantSpec variant_spec(int M, int prec, int v) {
       return v == 0 ? VariantSpec{1, {{1, 8}}, 128, 3, 0}
            : v == 1 ? VariantSpec{1, {{1, 8}}, 256, 1, 1}
            : v == 2 ? VariantSpec{2, {{1, 5}, {6, 8}}, 128, 2, 1}
-                    : VariantSpec{1, {{1, 8}}, 256, 1, 4};
+           : v == 3 ? VariantSpec{1, {{1, 8}}, 256, 1, 4}
+           : v == 4 ? VariantSpec{1, {{1, 8}}, 64, 6, 2}
+                    : VariantSpec{1, {{1, 8}}, 128, 3, 2};
     case 5:
       return v == 0 ? VariantSpec{1, {{1, 10}}, 256, 1, 1}
            : v == 1 ? VariantSpec{2, {{1, 7}, {8, 10}}, 128, 2, 1}
            : v == 2 ? VariantSpec{2, {{1, 7}, {8, 10}}, 256, 1, 1}
-                    : VariantSpec{1, {{1, 10}}, 256, 1, 4};
+           : v == 3 ? VariantSpec{1, {{1, 10}}, 256, 1, 4}
+           : v == 4 ? VariantSpec{1, {{1, 10}}, 64, 4, 2}
+                    : VariantSpec{1, {{1, 10}}, 128, 2, 2};
     case 6:
       return v == 0 ? VariantSpec{1, {{1, 12}}, 256, 1, 1}
            : v == 1 ? VariantSpec{2, {{1, 8}, {9, 12}}, 128, 2, 1}
            : v == 2 ? VariantSpec{3, {{1, 6}, {7, 9}, {10, 12}}, 128, 2, 1}
            : v == 3 ? VariantSpec{2, {{1, 8}, {9, 12}}, 256, 1, 1}
            : v == 4 ? VariantSpec{1, {{1, 12}}, 256, 1, 4}
-                    : VariantSpec{1, {{1, 12}}, 256, 1, 2};
+           : v == 5 ? VariantSpec{1, {{1, 12}}, 256, 1, 2}
+           : v == 6 ? VariantSpec{1, {{1, 12}}, 64, 4, 2}
+                    : VariantSpec{1, {{1, 12}}, 128, 2, 2};
     case 7:
       return v == 0 ? VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 1}
            : v == 1 ? VariantSpec{3, {{1, 7}, {8, 11}, {12, 14}}, 128, 2, 1}

@@ -2,7 +2,8 @@
 //  * prep:   core spreading lambda(t)^2 = lambda_0^2 + 4 nu t (eq:phi00) at the
 //            stage time, c = 2 lambda^2, and the source records
 //            (zeta = x / sqrt(c), a_m = M_m c^{-|m|/2}) for the pair kernel;
-//  * finish: sum of the pair partials over source chunks, the self pair from
+//  * finish: sum of the pair partials over source chunks, the Laplacian
+//            recursion that turns them into the correlation Psi, the self pair from
 //            the jet at the origin, the centroid velocity (eq:xjdot_Final, self
 //            pair excluded), the moment equation (eq:Final_CrossCoef with the
 //            (i,q) sums of eq:FinalSingleI/II folded into tables) including the
@@ -212,6 +213,17 @@ __device__ __forceinline__ void finish_block(const FinishArgs& A, int j0, double
       for (int ch = 0; ch < A.nchunks; ++ch) v += A.partial[((size_t)ch * NB + b) * A.n + j];
     }
     psi[idx] = v;
+  }
+  __syncthreads();
+  // 1b. the pair kernels leave Psi itself only in the edge columns beta1 <= 1;
+  //     a column beta1 >= 2 holds R[beta] = sum_m a_m D^{m + beta - 2 e1} Lap psi.
+  //     D_1^2 = Lap - D_2^2 gives Psi[beta] = R[beta] - Psi[beta - 2 e1 + 2 e2],
+  //     taken per order in increasing beta1.
+  const int BM = bmax_of(M);
+  for (int idx = threadIdx.x; idx < TB * BM; idx += blockDim.x) {
+    const int tt = idx / BM, k = idx % BM + 1;
+    double* ps = psi + tt * NB;
+    for (int b1 = 2; b1 <= k; ++b1) ps[bcol(b1, k - b1)] -= ps[bcol(b1 - 2, k - b1 + 2)];
   }
   for (int idx = threadIdx.x; idx < TB * K; idx += blockDim.x) {
     const int tt = idx / K, m = idx % K, p = j0 + tt;

@@ -244,14 +244,14 @@ def test_tile_expansions_match_full_jet(mm, order, kind):
         assert rhs_error(res["far"][1][rows], oM, order, wl.lam0) <= MIXED_RHS_TOL
 
 
-@pytest.mark.parametrize("order", [4, 6, 8])
+@pytest.mark.parametrize("order", [4, 5, 6, 7, 8])
 def test_every_kernel_variant(mm, order, monkeypatch):
     """Each compiled all-pairs variant reproduces the oracle (mixed precision)."""
     wl = mmvm_inputs.random_disk(n=300, order=order, radius=3.0, sigma=0.45, amp=0.02, moment_scale="absolute",
                                  seed=40 + order)
     ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu)
     seen = set()
-    for v in range(4):
+    for v in range(8):
         monkeypatch.setenv("MMVM_PAIR_VARIANT", str(v))
         ctx = mm.Context(order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32)
         try:
