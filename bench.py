@@ -29,8 +29,9 @@ served     the served stream (independent random-disk solves: n log-uniform in
            [64, 8192], M in {2, 4, 8}, Re uniform in [100, 5000], 50-500 RK4
            steps of 0.01) through the continuous-batching server: a burst
            (every request at t = 0) gives the saturation throughput, then
-           Poisson arrivals at 0.7x the saturation request rate give p50/p99
-           latency (submit -> result on the host; a request whose state leaves
+           Poisson arrivals at 0.7x and at 1.2x the saturation request rate
+           give p50/p99 latency below and above saturation (submit -> result
+           on the host; a request whose state leaves
            the finite range stops there with MMVM_E_NUMERIC and is counted
            apart); the smallest requests are
            re-run in the plain FP64 form (context API) for their error, and
@@ -341,15 +342,30 @@ def run_served(args, mm):
         return tot
 
     sat_rate = len(reqs) / span_b
-    lam = 0.7 * sat_rate
-    arrivals = [r.arrival / lam for r in reqs]  # the stream's own exponential gaps, rescaled
-    pois, span_p, st_p = _run_stream(mm, reqs, mixed, arrivals)
-    ok_p = [i for i, r in enumerate(pois) if _ok(r)]
-    lat = np.array([pois[i][2]["latency_ms"] for i in ok_p])
-    qms = np.array([pois[i][2]["queue_ms"] for i in ok_p])
-    diverged = [i for i, r in enumerate(pois) if r is not None and not _ok(r)
-                and "NUMERIC" in r[1]]
-    lat_div = np.array([pois[i][2].get("latency_ms", np.nan) for i in diverged])
+
+    def poisson(factor):
+        """The stream's own exponential gaps rescaled to factor x the
+        saturation request rate; latencies of the requests that finished."""
+        rate = factor * sat_rate
+        arrivals = [r.arrival / rate for r in reqs]
+        res, span, st = _run_stream(mm, reqs, mixed, arrivals)
+        ok = [i for i, r in enumerate(res) if _ok(r)]
+        lat = np.array([res[i][2]["latency_ms"] for i in ok])
+        qms = np.array([res[i][2]["queue_ms"] for i in ok])
+        div = [i for i, r in enumerate(res) if r is not None and not _ok(r)
+               and "NUMERIC" in r[1]]
+        lat_div = np.array([res[i][2].get("latency_ms", np.nan) for i in div])
+        return {"rate_per_s": rate, "of_saturation": factor, "makespan_s": span,
+                "value": done_work(res) / span, "unit": UNIT, "completed": len(ok),
+                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "mean_ms": float(lat.mean()) if len(lat) else None,
+                "queue_p50_ms": float(np.percentile(qms, 50)) if len(qms) else None,
+                "max_batch": st["max_batch"], "diverged": len(div),
+                "diverged_p50_ms": float(np.median(lat_div)) if len(lat_div) else None}
+
+    pois_under = poisson(0.7)
+    pois_over = poisson(1.2)
     # errors of the served mixed results against the plain FP64 form (context API)
     from tests.parity_util import state_error
 
@@ -383,16 +399,8 @@ def run_served(args, mm):
                        "unit": UNIT, "requests_per_s": sat_rate,
                        "completed": len(ok_b), "max_batch": st_b["max_batch"],
                        "ticks": st_b["ticks"]},
-        "poisson": {"rate_per_s": lam, "makespan_s": span_p,
-                    "value": done_work(pois) / span_p, "unit": UNIT,
-                    "completed": len(ok_p),
-                    "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
-                    "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
-                    "mean_ms": float(lat.mean()) if len(lat) else None,
-                    "queue_p50_ms": float(np.percentile(qms, 50)) if len(qms) else None,
-                    "max_batch": st_p["max_batch"],
-                    "diverged": len(diverged),
-                    "diverged_p50_ms": float(np.median(lat_div)) if len(lat_div) else None},
+        "poisson": pois_under,
+        "poisson_over_saturation": pois_over,
         "not_finite": [{"request": i, "n": reqs[i].workload.n, "order": reqs[i].workload.order,
                         "steps_done": burst[i][2].get("steps") if burst[i] else None,
                         "steps": reqs[i].workload.steps}
