@@ -27,6 +27,10 @@ are the benchmark configurations of this project):
   uniform in disks of radius 2 centred at (+-3, 0), circulations proportional
   to exp(-r^2) about the patch centre and normalised to 1 per patch, higher
   moments 0.
+* ``tripole_coarse_grid``: the coarse-grid tripole of Section 3.2.2: a
+  6 x 6 grid of centres on [-1, 1]^2, each particle's circulation the value
+  of the perturbed Lamb-Oseen vorticity of eq:perturbM2 at its node times the
+  node's area (eq:blurredIC), higher moments 0.
 * ``served_stream``: independent random_disk requests with log-uniform n,
   order drawn from {2,4,8}, Re uniform, step counts uniform, Poisson arrivals.
 
@@ -49,6 +53,7 @@ __all__ = [
     "random_disk",
     "two_patches",
     "served_stream",
+    "tripole_coarse_grid",
     "BASE_SEED",
 ]
 
@@ -212,3 +217,32 @@ def served_stream(count: int = 2000, rate: float = 1.0, seed: int = BASE_SEED + 
                          seed=seed * 1000 + i)
         out.append(Request(i, t, wl))
     return out
+
+
+def tripole_coarse_grid(order: int = 2, delta: float = 0.25, lam0: float = 1.0,
+                        Re: float = 1000.0, nodes: int = 6, half_width: float = 1.0,
+                        dt: float = 0.01, steps: int = 1600) -> Workload:
+    """Coarse-grid approximation of a large quadrupole perturbation of the
+    Lamb-Oseen vortex (Section 3.2.2).
+
+    The initial vorticity is eq:perturbM2, phi_00 + 4 delta (phi_20 - phi_02)
+    with phi_k = D^k phi_00 and phi_00 = exp(-|x|^2/lam0^2) / (pi lam0^2);
+    written out, omega_0(x) = phi_00(x) (1 + 16 delta (x1^2 - x2^2) / lam0^4).
+    The centres form a uniform nodes x nodes grid on [-half_width,
+    half_width]^2, end points included; every node carries the area h^2
+    (h the node spacing) and the circulation M^j[0,0] = omega_0(x_j) h^2
+    (eq:blurredIC); all other moments are 0.  Every particle has the core
+    lam0, the core of the expansion.  Deterministic (no random draws).
+    """
+    g = np.linspace(-half_width, half_width, nodes)
+    h = g[1] - g[0]
+    X1, X2 = np.meshgrid(g, g, indexing="ij")
+    x = np.stack([X1.ravel(), X2.ravel()], axis=1)
+    r2 = x[:, 0] ** 2 + x[:, 1] ** 2
+    phi00 = np.exp(-r2 / lam0 ** 2) / (math.pi * lam0 ** 2)
+    omega0 = phi00 * (1.0 + 16.0 * delta * (x[:, 0] ** 2 - x[:, 1] ** 2) / lam0 ** 4)
+    m = np.zeros((x.shape[0], n_moments(order)))
+    m[:, 0] = omega0 * h * h
+    return Workload(x, m, order, lam0, 1.0 / Re, dt, steps,
+                    name=f"coarse-grid tripole {nodes}x{nodes} M={order} delta={delta}",
+                    meta={"delta": delta, "Re": Re, "node_area": h * h})

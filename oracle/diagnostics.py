@@ -15,6 +15,9 @@ Test infrastructure only (see ``oracle/__init__.py``).
       <omega>(r) = (1/2pi) int_0^{2pi} omega(c + r e_theta) dtheta,
   about a centre c, on a polar grid: the trapezoid rule in theta (spectrally
   accurate for a periodic integrand) and Gauss-Legendre in r on [0, r_max].
+* The single-particle expansion of a set of Gaussian vortices (the reference
+  of the coarse-grid tripole, Section 3.2.2) and the relative L2 / L-infinity
+  errors of a sampled vorticity field (Section 4.2, Table 1).
 """
 from __future__ import annotations
 
@@ -73,3 +76,31 @@ def nonaxi_enstrophy(x, moments, lam, order, cx=0.0, cy=0.0, r_max=None, nr=96,
     w = vorticity(x, moments, lam, order, pts).reshape(nr, ntheta)
     dev = w - w.mean(axis=1, keepdims=True)
     return float(np.sum(wr * (dev ** 2).sum(axis=1)) * dth)
+
+
+def shifted_gaussians_expansion(x: np.ndarray, m00: np.ndarray, order: int,
+                                centre=(0.0, 0.0)) -> np.ndarray:
+    """Moments (1, K) about `centre` of the field sum_j m00_j phi_00(p - x^j)
+    in the basis D^k phi_00 of the same core (the single-particle form of a
+    set of Gaussian vortices, as the order-24 reference of Section 3.2.2
+    uses).  Taylor's theorem in the shift a_j = x^j - centre gives, for every
+    core, phi_00(p - a) = sum_k (-a)^k / k! D^k phi_00(p), so
+        M_k = sum_j m00_j (-a_j1)^k1 (-a_j2)^k2 / (k1! k2!),
+    exact up to the truncation at total order `order`."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    a = x - np.asarray(centre, dtype=np.float64)
+    m00 = np.asarray(m00, dtype=np.float64).ravel()
+    mi = multi_indices(order)
+    out = np.zeros((1, len(mi)))
+    for col, (k1, k2) in enumerate(mi):
+        out[0, col] = np.sum(m00 * (-a[:, 0]) ** k1 * (-a[:, 1]) ** k2) / (
+            math.factorial(k1) * math.factorial(k2))
+    return out
+
+
+def relative_errors(w: np.ndarray, w_ref: np.ndarray) -> tuple:
+    """(relative L2, relative L-infinity) error of the sampled field w against
+    w_ref on the same uniform grid (Section 4.2): ||w - w_ref|| / ||w_ref||."""
+    d = np.asarray(w) - np.asarray(w_ref)
+    return (float(np.linalg.norm(d) / np.linalg.norm(w_ref)),
+            float(np.abs(d).max() / np.abs(w_ref).max()))
