@@ -31,6 +31,8 @@ are the benchmark configurations of this project):
   6 x 6 grid of centres on [-1, 1]^2, each particle's circulation the value
   of the perturbed Lamb-Oseen vorticity of eq:perturbM2 at its node times the
   node's area (eq:blurredIC), higher moments 0.
+* ``vortex_pair``: two equal Gaussian vortices of circulation 1 at
+  (+-b/2, 0) with core a (Section 3.2.1, vortex merger), higher moments 0.
 * ``served_stream``: independent random_disk requests with log-uniform n,
   order drawn from {2,4,8}, Re uniform, step counts uniform, Poisson arrivals.
 
@@ -54,6 +56,7 @@ __all__ = [
     "two_patches",
     "served_stream",
     "tripole_coarse_grid",
+    "vortex_pair",
     "BASE_SEED",
 ]
 
@@ -246,3 +249,17 @@ def tripole_coarse_grid(order: int = 2, delta: float = 0.25, lam0: float = 1.0,
     return Workload(x, m, order, lam0, 1.0 / Re, dt, steps,
                     name=f"coarse-grid tripole {nodes}x{nodes} M={order} delta={delta}",
                     meta={"delta": delta, "Re": Re, "node_area": h * h})
+
+
+def vortex_pair(order: int = 6, a_over_b: float = 0.375, b: float = 2.0,
+                Re: float = 1000.0, dt: float = 0.01, steps: int = 1200) -> Workload:
+    """Two equal co-rotating Gaussian vortices (Section 3.2.1, vortex
+    merger): centres (-b/2, 0) and (b/2, 0), circulation M[0,0] = 1 each,
+    core lambda_0 = a = a_over_b * b (the radius in exp(-r^2/a^2)), higher
+    moments 0, nu = 1/Re.  Deterministic."""
+    x = np.array([[-0.5 * b, 0.0], [0.5 * b, 0.0]])
+    m = np.zeros((2, n_moments(order)))
+    m[:, 0] = 1.0
+    return Workload(x, m, order, a_over_b * b, 1.0 / Re, dt, steps,
+                    name=f"vortex pair a/b={a_over_b} M={order}",
+                    meta={"a_over_b": a_over_b, "b": b, "Re": Re})
