@@ -123,13 +123,14 @@ struct mmvm_ctx {
 
 namespace {
 
-int choose_chunks(const mmvm_ctx* c, int64_t n) {
+// Source chunks of an all-pairs launch over n records with tpc targets per
+// CTA and per_sm resident CTAs per SM.
+int chunks_for(int64_t n, int tpc, int per_sm, int device, int S) {
   if (n <= 1) return 0;
   int dev_sms = 0;
-  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
-  int per_sm = c->pe.nslices ? mmvm::pair_occupancy(c->pe, c->S) : 1;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device);
   per_sm = std::max(per_sm, 1);
-  const int64_t tiles = (n + c->pe.tpc - 1) / c->pe.tpc;
+  const int64_t tiles = (n + tpc - 1) / tpc;
   const int64_t slots = (int64_t)std::max(dev_sms, 1) * per_sm;
   // ~48 waves of CTAs, chunks no shorter than 4 tiles of sources: target
   // tiles differ a lot in cost (near vs far tiles), and many small CTAs let
@@ -138,10 +139,19 @@ int choose_chunks(const mmvm_ctx* c, int64_t n) {
   // 48 chunks 217 ms per launch)
   int64_t ch = (48 * slots + tiles - 1) / tiles;
   if (const char* f = std::getenv("MMVM_CHUNKS")) ch = std::atoi(f);  // measurement override
-  const int64_t max_ch = std::max<int64_t>(1, n / (4 * c->S));
+  const int64_t max_ch = std::max<int64_t>(1, n / (4 * S));
   ch = std::min(std::max<int64_t>(ch, 1), max_ch);
   return (int)ch;
 }
+
+int choose_chunks(const mmvm_ctx* c, int64_t n) {
+  const int per_sm = c->pe.nslices ? mmvm::pair_occupancy(c->pe, c->S) : 1;
+  return chunks_for(n, c->pe.tpc, per_sm, c->cfg.device, c->S);
+}
+
+// Chunks a variant is timed on by the autotuner (the partial buffer always
+// holds at least this many).
+constexpr int kTuneChunks = 8;
 
 // Process-wide autotuning results: (device, M, precision, far, log2 n) -> variant.
 std::mutex g_tune_mu;
@@ -174,7 +184,7 @@ int ensure_buffers(mmvm_ctx* c, int64_t n) {
   if (n > 1) {
     c->chunks = choose_chunks(c, n);
     MMVM_CK(grow(c->rec, (size_t)n * c->pe.rec_len * c->pe.elem_bytes));
-    MMVM_CK(grow(c->partial, (size_t)std::max(c->chunks, 4) * c->NB * n));
+    MMVM_CK(grow(c->partial, (size_t)std::max(c->chunks, kTuneChunks) * c->NB * n));
     if (c->far) {
       MMVM_CK(grow(c->perm, (size_t)n));
       MMVM_CK(grow(c->gbox, (size_t)mmvm::gdata_len(c->M) *
@@ -316,7 +326,7 @@ int enqueue_step(mmvm_ctx* c) {
 
 // Pick the all-pairs variant for this (order, precision, size class): time
 // each compiled variant on the current records (every target tile against the
-// first few 1024-source chunks, at least two waves of CTAs) and keep the
+// first kTuneChunks source chunks of the variant's own chunking) and keep the
 // fastest per pair.  MMVM_PAIR_VARIANT=<v> forces a variant, MMVM_AUTOTUNE=0
 // keeps variant 0.  Runs outside any stream capture (from set_state).
 int tune_pair(mmvm_ctx* c) {
@@ -346,8 +356,6 @@ int tune_pair(mmvm_ctx* c) {
     MMVM_CK(mmvm::launch_prep(c->cfg.precision, n, c->M, perm, c->x.p, c->m.p, c->t_dev(),
                               nullptr, 0.0, lam0sq, four_nu, c->rec.p,
                               c->far ? c->gbox.p : nullptr, c->st));
-    int dev_sms = 0;
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
     cudaEvent_t e0, e1;
     MMVM_CK(cudaEventCreate(&e0));
     MMVM_CK(cudaEventCreate(&e1));
@@ -362,10 +370,11 @@ int tune_pair(mmvm_ctx* c) {
       }
       const int per_sm = mmvm::pair_occupancy(e, c->S);
       if (per_sm < 1) continue;
-      const int tiles = (n + e.tpc - 1) / e.tpc;
-      const int chunks = std::max(1, n / 1024);
+      // the production chunking of this variant, first kTuneChunks chunks
+      // (many waves of CTAs, so the tail does not decide)
+      const int chunks = std::max(1, chunks_for(n, e.tpc, per_sm, c->cfg.device, c->S));
       const int chunk_len = mmvm::round_up((n + chunks - 1) / chunks, c->S);
-      const int gy = std::min({chunks, 4, std::max(1, (2 * dev_sms * per_sm + tiles - 1) / tiles)});
+      const int gy = std::min(chunks, kTuneChunks);
       const void* gb = c->far ? c->gbox.p : nullptr;
       MMVM_CK(mmvm::pair_launch(e, c->rec.p, n, chunks, c->S, gb, c->partial.p, gy, c->st));
       MMVM_CK(cudaEventRecord(e0, c->st));

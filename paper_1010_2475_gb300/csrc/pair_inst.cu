@@ -19,14 +19,15 @@ constexpr VariantSpec kSpec = variant_spec(kM, MMVM_INST_PREC, MMVM_INST_V);
 static_assert(MMVM_INST_S < kSpec.nslices, "slice index out of range");
 constexpr int kLO = kSpec.s[MMVM_INST_S].lo;
 constexpr int kHI = kSpec.s[MMVM_INST_S].hi;
+constexpr int kPART = kSpec.s[MMVM_INST_S].part;
 constexpr int kTPC = kSpec.TPC;
 constexpr int kMINB = kSpec.MINB;
 constexpr int kSYNC = kSpec.SYNC;
 static_assert(kTPC % 32 == 0, "targets per CTA must be whole warps");
-#define MMVM_KERNEL pair_kernel<kM, T, kLO, kHI, kTPC, kMINB, kSYNC>
-#define MMVM_BATCH_KERNEL pair_batch_kernel<kM, T, kLO, kHI, kTPC, kMINB, kSYNC>
+#define MMVM_KERNEL pair_kernel<kM, T, kLO, kHI, kPART, kTPC, kMINB, kSYNC>
+#define MMVM_BATCH_KERNEL pair_batch_kernel<kM, T, kLO, kHI, kPART, kTPC, kMINB, kSYNC>
 
-size_t smem_fn(int S) { return pair_smem_bytes<kM, T, kLO, kHI, kTPC>(S); }
+size_t smem_fn(int S) { return pair_smem_bytes<kM, T, kLO, kHI, kPART, kTPC>(S); }
 cudaError_t prepare_fn(int S) {
   cudaError_t e = cudaFuncSetAttribute(MMVM_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_fn(S));

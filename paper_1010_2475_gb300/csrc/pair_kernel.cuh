@@ -98,8 +98,10 @@ __device__ __forceinline__ T kummer_sum(T x) {
 }
 
 // Outputs of one order slice: Psi[beta] with LO <= |beta| <= HI, i.e. the
-// columns [B0, B1).  They need the jet orders LO .. HI + M only.
-template <int M, typename T, int LO, int HI>
+// columns [B0, B1).  They need the jet orders LO .. HI + M only.  PART 1
+// accumulates only the edge columns (the jet), PART 2 only the Laplacian
+// columns (Hermite functions, no jet), PART 0 both.
+template <int M, typename T, int LO, int HI, int PART = 0>
 struct PairNear {
   static constexpr int K = n_moments(M);
   static constexpr int NB = n_beta(M);
@@ -155,6 +157,7 @@ struct PairNear {
       hy[k] = fma(l2, hy[k + 1], hy[k]);
     });
 
+    if constexpr (PART != 2) {
     // w[n-1] = zbar^n I_{n-1}(x), n = 1..NJ
     T wr[NJ], wi[NJ];
     if (x < T(40)) {
@@ -274,10 +277,11 @@ struct PairNear {
         acc[bcol(1, kd - 1) - B0] += pe[2 * (kd - LO) + 1];
       }
     });
+    }  // PART != 2
     // Laplacian columns (beta1 >= 2): R[beta] = sum_m a_m e_(m + beta - 2 e1),
     // taken one gamma2 = beta2 at a time as sum_m1 hx[m1 + gamma1] T[m1] with
     // T[m1] = sum_m2 a_(m1, m2) hy[m2 + gamma2] (the Gaussian jet is separable).
-    if constexpr (GHI >= 0) {
+    if constexpr (GHI >= 0 && PART != 1) {
       static_for<0, GHI + 1>([&](auto g2c) {
         constexpr int g2 = decltype(g2c)::value;
         T tq[M + 1];

@@ -26,10 +26,10 @@ namespace mmvm {
 
 // One near-field source.  acc points at the register array of the slice;
 // every index used is a compile-time constant after inlining.
-template <int M, typename T, int LO, int HI>
+template <int M, typename T, int LO, int HI, int PART>
 __device__ __forceinline__ void near_source(const T* r, int src, int j, T tz1, T tz2, T tl1,
                                             T tl2, T* acc) {
-  using PN = PairNear<M, T, LO, HI>;
+  using PN = PairNear<M, T, LO, HI, PART>;
   constexpr int K = n_moments(M);
   constexpr int HDR = Rec<T>::HDR;
   T (&accr)[PN::NBL] = *reinterpret_cast<T(*)[PN::NBL]>(acc);
@@ -72,24 +72,54 @@ __device__ __forceinline__ void flush_one(float& v, float* acc_hi, float* acc_lo
   v = 0.f;
 }
 
-// Fold FP32 register sums into this thread's shared-memory (hi, lo) pairs.
-template <int NBL, int TPC>
-__device__ __forceinline__ void flush_sums(float* acc, float* acc_hi, float* acc_lo, int slot) {
-#pragma unroll
-  for (int b = 0; b < NBL; ++b) flush_one(acc[b], acc_hi, acc_lo, b * TPC + slot);
+// beta1 of correlation column col (col = bcol(b1, b2)).
+__host__ __device__ constexpr int col_beta1(int col) {
+  int k = 1;
+  while (tri(k + 1) - 1 <= col) ++k;
+  return k - (col + 1 - tri(k));
 }
 
-// The same for the edge columns (beta1 in {0, 1}) of a slice only: the far
-// field writes nothing else.
-template <int M, int LO, int HI, int TPC>
+// The columns of slice [LO, HI] that part PART accumulates (see SliceSpec),
+// numbered from the slice's first column, and their compact shared-memory
+// slots: column c of the slice sits at slot(c).
+template <int LO, int HI, int PART>
+struct PartCols {
+  static constexpr int B0 = tri(LO) - 1;
+  static constexpr int NBL = tri(HI + 1) - 1 - B0;
+  __host__ __device__ static constexpr bool in(int c) {
+    return PART == 0 || ((col_beta1(c + B0) <= 1) == (PART == 1));
+  }
+  __host__ __device__ static constexpr int slot(int c) {
+    int s = 0;
+    for (int i = 0; i < c; ++i) s += in(i) ? 1 : 0;
+    return s;
+  }
+  static constexpr int NS = slot(NBL);  // slots in use
+};
+
+// Fold this part's FP32 register sums into this thread's shared-memory
+// (hi, lo) pairs.
+template <int LO, int HI, int PART, int TPC>
+__device__ __forceinline__ void flush_sums(float* acc, float* acc_hi, float* acc_lo, int slot) {
+  using PC = PartCols<LO, HI, PART>;
+  static_for<0, PC::NBL>([&](auto cc) {
+    constexpr int c = decltype(cc)::value;
+    if constexpr (PC::in(c)) flush_one(acc[c], acc_hi, acc_lo, PC::slot(c) * TPC + slot);
+  });
+}
+
+// The same for the edge columns (beta1 in {0, 1}) only: the far field writes
+// nothing else.
+template <int M, int LO, int HI, int PART, int TPC>
 __device__ __forceinline__ void flush_edge_sums(float* acc, float* acc_hi, float* acc_lo,
                                                 int slot) {
-  constexpr int B0 = PairNear<M, float, LO, HI>::B0;
+  using PC = PartCols<LO, HI, PART>;
+  static_assert(PART != 2, "the Laplacian part has no edge columns");
   static_for<LO, HI + 1>([&](auto nbc) {
     constexpr int nb = decltype(nbc)::value;
-    constexpr int c0 = bcol(0, nb) - B0, c1 = bcol(1, nb - 1) - B0;
-    flush_one(acc[c0], acc_hi, acc_lo, c0 * TPC + slot);
-    flush_one(acc[c1], acc_hi, acc_lo, c1 * TPC + slot);
+    constexpr int c0 = bcol(0, nb) - PC::B0, c1 = bcol(1, nb - 1) - PC::B0;
+    flush_one(acc[c0], acc_hi, acc_lo, PC::slot(c0) * TPC + slot);
+    flush_one(acc[c1], acc_hi, acc_lo, PC::slot(c1) * TPC + slot);
   });
 }
 
@@ -151,20 +181,21 @@ __device__ __forceinline__ bool tile_takes_m2p(const float* __restrict__ gdata, 
 // evaluated, pairs they cover), added by the first slice only.  Called by every thread of the CTA; begins by writing only its
 // own shared-memory slots and reuses the tile only after a barrier, so a
 // persistent CTA may call it for one item after another.
-template <int M, typename T, int LO, int HI, int TPC, int SYNC>
+template <int M, typename T, int LO, int HI, int PART, int TPC, int SYNC>
 __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n, int tile0, int c0,
                                                int c1, int S, const float* __restrict__ gdata,
                                                double* __restrict__ out,
                                                unsigned long long* __restrict__ counts,
                                                unsigned char* smem_raw) {
-  using PN = PairNear<M, T, LO, HI>;
+  using PN = PairNear<M, T, LO, HI, PART>;
+  using PC = PartCols<LO, HI, PART>;
   constexpr int R = rec_len<T>(M);
   constexpr int NBL = PN::NBL;
   constexpr int NY = HI - LO + 1;
   constexpr bool f32 = std::is_same<T, float>::value;
   T* tile = reinterpret_cast<T*>(smem_raw);
   float* acc_hi = reinterpret_cast<float*>(tile + (size_t)S * R);
-  float* acc_lo = acc_hi + NBL * TPC;
+  float* acc_lo = acc_hi + PC::NS * TPC;
   const int warp = threadIdx.x >> 5;
   const int slot = threadIdx.x;
   const int j = tile0 + slot;
@@ -185,8 +216,10 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
 #pragma unroll
   for (int b = 0; b < NBL; ++b) acc[b] = T(0);
   if constexpr (f32) {
-    for (int i = threadIdx.x; i < 2 * NBL * TPC; i += blockDim.x) acc_hi[i] = 0.f;
+    for (int i = threadIdx.x; i < 2 * PC::NS * TPC; i += blockDim.x) acc_hi[i] = 0.f;
   }
+  // far tiles: skipped by every part; summed (pass 1) by parts 0 and 1 (the
+  // Laplacian columns of a far tile are zero)
   const bool use_far = f32 && gdata != nullptr;
   // this thread's target: pairs on each path, tile expansions evaluated
   unsigned n_near = 0, n_far = 0, n_m2p = 0, n_m2p_pairs = 0;
@@ -202,7 +235,7 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
     int4* dst = reinterpret_cast<int4*>(tile);
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
   };
-  if constexpr (f32) {
+  if constexpr (f32 && PART != 2) {
     if (use_far) {
       // pass 1: far tiles (tiles start at multiples of kGroup: chunk_len is a
       // multiple of S = kGroup)
@@ -234,7 +267,7 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
 #pragma unroll
           for (int b = 0; b < NBL; ++b) tmp[b] = 0.f;
           fold_far<M, float, LO, HI>(yr, yi, tmp);
-          flush_edge_sums<M, LO, HI, TPC>(tmp, acc_hi, acc_lo, slot);
+          flush_edge_sums<M, LO, HI, PART, TPC>(tmp, acc_hi, acc_lo, slot);
           if (j < n) {
             n_m2p += 1;
             n_m2p_pairs += cnt;
@@ -264,7 +297,7 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
 #pragma unroll
             for (int b = 0; b < NBL; ++b) tmp[b] = 0.f;
             fold_far<M, float, LO, HI>(yr, yi, tmp);
-            flush_edge_sums<M, LO, HI, TPC>(tmp, acc_hi, acc_lo, slot);
+            flush_edge_sums<M, LO, HI, PART, TPC>(tmp, acc_hi, acc_lo, slot);
           }
         }
       }
@@ -284,17 +317,18 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
       __syncthreads();
 #pragma unroll 1
       for (int s = 0; s < cnt; ++s) {
-        if (near) near_source<M, T, LO, HI>(tile + s * R, t0 + s, j, tz1, tz2, tl1, tl2, acc);
+        if (near)
+          near_source<M, T, LO, HI, PART>(tile + s * R, t0 + s, j, tz1, tz2, tl1, tl2, acc);
         if constexpr (SYNC > 0) {
               if (s % SYNC == SYNC - 1 || s == cnt - 1) __syncthreads();  // CTA-uniform
             }
       }
       if constexpr (f32) {
-        if (near) flush_sums<NBL, TPC>(acc, acc_hi, acc_lo, slot);
+        if (near) flush_sums<LO, HI, PART, TPC>(acc, acc_hi, acc_lo, slot);
       }
     }
   }
-  if (LO == 1 && counts != nullptr) {
+  if (LO == 1 && PART != 2 && counts != nullptr) {
     const unsigned wn = __reduce_add_sync(0xffffffffu, n_near);
     const unsigned wf = __reduce_add_sync(0xffffffffu, n_far);
     const unsigned we = __reduce_add_sync(0xffffffffu, n_m2p);
@@ -308,22 +342,25 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
   }
   if (j < n) {
     double* o = out + (size_t)PN::B0 * n + j;
-#pragma unroll
-    for (int b = 0; b < NBL; ++b) {
-      double v;
-      if constexpr (f32) {
-        v = (double)acc_hi[b * TPC + slot] + (double)acc_lo[b * TPC + slot];
-      } else {
-        v = acc[b];
+    static_for<0, NBL>([&](auto bc) {
+      constexpr int b = decltype(bc)::value;
+      if constexpr (PC::in(b)) {
+        double v;
+        if constexpr (f32) {
+          constexpr int q = PC::slot(b) * TPC;
+          v = (double)acc_hi[q + slot] + (double)acc_lo[q + slot];
+        } else {
+          v = acc[b];
+        }
+        o[(size_t)b * n] = v;
       }
-      o[(size_t)b * n] = v;
-    }
+    });
   }
 }
 
 // One context: grid (target tiles, source chunks) over n records.
 // Layout of `partial`: [chunk][beta column][target] FP64.
-template <int M, typename T, int LO, int HI, int TPC, int MINB, int SYNC>
+template <int M, typename T, int LO, int HI, int PART, int TPC, int MINB, int SYNC>
 __global__ void __launch_bounds__(TPC, MINB)
     pair_kernel(const T* __restrict__ rec, int n, int chunk_len, int S,
                 const float* __restrict__ gdata, double* __restrict__ partial,
@@ -332,7 +369,7 @@ __global__ void __launch_bounds__(TPC, MINB)
   constexpr int NB = n_beta(M);
   const int c0 = blockIdx.y * chunk_len;
   const int c1 = min(n, c0 + chunk_len);
-  pair_tile_work<M, T, LO, HI, TPC, SYNC>(rec, n, blockIdx.x * TPC, c0, c1, S, gdata,
+  pair_tile_work<M, T, LO, HI, PART, TPC, SYNC>(rec, n, blockIdx.x * TPC, c0, c1, S, gdata,
                                           partial + (size_t)blockIdx.y * NB * n, counts,
                                           smem_raw);
 }
@@ -343,7 +380,7 @@ __global__ void __launch_bounds__(TPC, MINB)
 // The counter must be zero at launch (the caller clears it).  gdata (null: no
 // far field) holds the group records of the whole batch (instances start on
 // group boundaries).
-template <int M, typename T, int LO, int HI, int TPC, int MINB, int SYNC>
+template <int M, typename T, int LO, int HI, int PART, int TPC, int MINB, int SYNC>
 __global__ void __launch_bounds__(TPC, MINB)
     pair_batch_kernel(const T* __restrict__ rec, const BatchInst* __restrict__ inst,
                       const int4* __restrict__ items, const int* __restrict__ n_items,
@@ -365,7 +402,7 @@ __global__ void __launch_bounds__(TPC, MINB)
     const BatchInst ip = inst[w.x];
     const int c0 = w.z * ip.chunk_len;
     const int c1 = min(ip.n, c0 + ip.chunk_len);
-    pair_tile_work<M, T, LO, HI, TPC, SYNC>(rec + (size_t)ip.slot0 * R, ip.n, w.y, c0, c1, S,
+    pair_tile_work<M, T, LO, HI, PART, TPC, SYNC>(rec + (size_t)ip.slot0 * R, ip.n, w.y, c0, c1, S,
                                             gdata ? group_rec<M>(gdata, ip.slot0 / kGroup)
                                                   : nullptr,
                                             partial + ip.part_off + (size_t)w.z * NB * ip.n,
@@ -373,11 +410,11 @@ __global__ void __launch_bounds__(TPC, MINB)
   }
 }
 
-template <int M, typename T, int LO, int HI, int TPC>
+template <int M, typename T, int LO, int HI, int PART, int TPC>
 size_t pair_smem_bytes(int S) {  // shared memory of one CTA
   size_t b = (size_t)S * rec_len<T>(M) * sizeof(T);
   if (std::is_same<T, float>::value)
-    b += 2 * (size_t)PairNear<M, T, LO, HI>::NBL * TPC * sizeof(float);
+    b += 2 * (size_t)PartCols<LO, HI, PART>::NS * TPC * sizeof(float);
   return b;
 }
 

@@ -10,11 +10,16 @@
 
 namespace mmvm {
 
+// part: which columns of the orders lo..hi the kernel accumulates.
+// 0: all of them; 1: the edge columns beta1 <= 1 (the jet, and the far
+// field); 2: the Laplacian columns beta1 >= 2 (Hermite functions only, near
+// tiles only).  A variant that splits a range lists it once per part.
 struct SliceSpec {
-  int lo, hi;
+  int lo = 0, hi = 0;
+  int part = 0;
 };
 
-constexpr int kMaxVariants = 8;
+constexpr int kMaxVariants = 10;
 constexpr int kMaxSlices = 4;
 
 struct VariantSpec {
@@ -25,7 +30,7 @@ struct VariantSpec {
 
 constexpr int n_variants(int M, int prec) {
   if (prec == 0) return 1;
-  return M <= 3 ? 1 : (M == 7 ? 3 : (M == 6 ? 8 : (M == 8 ? 4 : 6)));
+  return M <= 3 ? 1 : (M == 7 ? 3 : (M == 6 ? 10 : (M == 8 ? 4 : 6)));
 }
 
 constexpr VariantSpec variant_spec(int M, int prec, int v) {
@@ -69,7 +74,9 @@ constexpr VariantSpec variant_spec(int M, int prec, int v) {
            : v == 4 ? VariantSpec{1, {{1, 12}}, 256, 1, 4}
            : v == 5 ? VariantSpec{1, {{1, 12}}, 256, 1, 2}
            : v == 6 ? VariantSpec{1, {{1, 12}}, 64, 4, 2}
-                    : VariantSpec{1, {{1, 12}}, 128, 2, 2};
+           : v == 7 ? VariantSpec{1, {{1, 12}}, 128, 2, 2}
+           : v == 8 ? VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 128, 3, 1}
+                    : VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 128, 4, 1};
     case 7:
       return v == 0 ? VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 1}
            : v == 1 ? VariantSpec{3, {{1, 7}, {8, 11}, {12, 14}}, 128, 2, 1}
