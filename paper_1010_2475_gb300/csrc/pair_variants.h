@@ -30,7 +30,7 @@ struct VariantSpec {
 
 constexpr int n_variants(int M, int prec) {
   if (prec == 0) return 1;
-  return M <= 3 ? 1 : (M == 7 ? 3 : (M == 6 ? 10 : (M == 8 ? 4 : 6)));
+  return M <= 3 ? 1 : (M == 7 ? 5 : (M == 6 ? 10 : (M == 8 ? 6 : 8)));
 }
 
 constexpr VariantSpec variant_spec(int M, int prec, int v) {
@@ -58,14 +58,18 @@ constexpr VariantSpec variant_spec(int M, int prec, int v) {
            : v == 2 ? VariantSpec{2, {{1, 5}, {6, 8}}, 128, 2, 1}
            : v == 3 ? VariantSpec{1, {{1, 8}}, 256, 1, 4}
            : v == 4 ? VariantSpec{1, {{1, 8}}, 64, 6, 2}
-                    : VariantSpec{1, {{1, 8}}, 128, 3, 2};
+           : v == 5 ? VariantSpec{1, {{1, 8}}, 128, 3, 2}
+           : v == 6 ? VariantSpec{2, {{1, 8, 1}, {1, 8, 2}}, 128, 4, 1}
+                    : VariantSpec{2, {{1, 8, 1}, {1, 8, 2}}, 128, 5, 1};
     case 5:
       return v == 0 ? VariantSpec{1, {{1, 10}}, 256, 1, 1}
            : v == 1 ? VariantSpec{2, {{1, 7}, {8, 10}}, 128, 2, 1}
            : v == 2 ? VariantSpec{2, {{1, 7}, {8, 10}}, 256, 1, 1}
            : v == 3 ? VariantSpec{1, {{1, 10}}, 256, 1, 4}
            : v == 4 ? VariantSpec{1, {{1, 10}}, 64, 4, 2}
-                    : VariantSpec{1, {{1, 10}}, 128, 2, 2};
+           : v == 5 ? VariantSpec{1, {{1, 10}}, 128, 2, 2}
+           : v == 6 ? VariantSpec{2, {{1, 10, 1}, {1, 10, 2}}, 128, 3, 1}
+                    : VariantSpec{2, {{1, 10, 1}, {1, 10, 2}}, 128, 4, 1};
     case 6:
       return v == 0 ? VariantSpec{1, {{1, 12}}, 256, 1, 1}
            : v == 1 ? VariantSpec{2, {{1, 8}, {9, 12}}, 128, 2, 1}
@@ -80,12 +84,16 @@ constexpr VariantSpec variant_spec(int M, int prec, int v) {
     case 7:
       return v == 0 ? VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 1}
            : v == 1 ? VariantSpec{3, {{1, 7}, {8, 11}, {12, 14}}, 128, 2, 1}
-                    : VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 4};
+           : v == 2 ? VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 4}
+           : v == 3 ? VariantSpec{3, {{1, 14, 1}, {1, 10, 2}, {11, 14, 2}}, 128, 3, 1}
+                    : VariantSpec{2, {{1, 14, 1}, {1, 14, 2}}, 128, 2, 1};
     default:
       return v == 0 ? VariantSpec{3, {{1, 8}, {9, 12}, {13, 16}}, 128, 2, 1}
            : v == 1 ? VariantSpec{4, {{1, 8}, {9, 11}, {12, 14}, {15, 16}}, 128, 2, 1}
            : v == 2 ? VariantSpec{4, {{1, 8}, {9, 11}, {12, 14}, {15, 16}}, 256, 1, 1}
-                    : VariantSpec{3, {{1, 8}, {9, 12}, {13, 16}}, 128, 2, 4};
+           : v == 3 ? VariantSpec{3, {{1, 8}, {9, 12}, {13, 16}}, 128, 2, 4}
+           : v == 4 ? VariantSpec{3, {{1, 16, 1}, {1, 12, 2}, {13, 16, 2}}, 128, 3, 1}
+                    : VariantSpec{3, {{1, 16, 1}, {1, 12, 2}, {13, 16, 2}}, 128, 2, 1};
   }
 }
 
