@@ -19,7 +19,7 @@ struct SliceSpec {
   int part = 0;
 };
 
-constexpr int kMaxVariants = 10;
+constexpr int kMaxVariants = 11;
 constexpr int kMaxSlices = 4;
 
 struct VariantSpec {
@@ -30,7 +30,7 @@ struct VariantSpec {
 
 constexpr int n_variants(int M, int prec) {
   if (prec == 0) return 1;
-  return M <= 3 ? 1 : (M == 7 ? 5 : (M == 6 ? 10 : (M == 8 ? 6 : 8)));
+  return M <= 3 ? 1 : (M == 7 ? 5 : (M == 6 ? 11 : (M == 8 ? 6 : 8)));
 }
 
 constexpr VariantSpec variant_spec(int M, int prec, int v) {
@@ -80,7 +80,8 @@ constexpr VariantSpec variant_spec(int M, int prec, int v) {
            : v == 6 ? VariantSpec{1, {{1, 12}}, 64, 4, 2}
            : v == 7 ? VariantSpec{1, {{1, 12}}, 128, 2, 2}
            : v == 8 ? VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 128, 3, 1}
-                    : VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 128, 4, 1};
+           : v == 9 ? VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 128, 4, 1}
+                     : VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 384, 1, 1};
     case 7:
       return v == 0 ? VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 1}
            : v == 1 ? VariantSpec{3, {{1, 7}, {8, 11}, {12, 14}}, 128, 2, 1}

@@ -251,7 +251,7 @@ def test_every_kernel_variant(mm, order, monkeypatch):
                                  seed=40 + order)
     ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu)
     seen = set()
-    for v in range(10):
+    for v in range(11):
         monkeypatch.setenv("MMVM_PAIR_VARIANT", str(v))
         ctx = mm.Context(order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32)
         try:
