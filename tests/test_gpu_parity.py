@@ -157,14 +157,33 @@ def test_random_disk_full_size_sampled_rows(mm, prec):
     assert rhs_error(gM[rows], oM, wl.order, wl.lam0) <= tol
 
 
-def test_two_patches_full_size_sampled_rows(mm):
-    """N = 65536, M = 6 two patches (mixed precision): sampled rows vs oracle."""
+@pytest.fixture(scope="module")
+def two_patches_rows():
+    """The benchmark workload and the oracle's right-hand side on 4 sampled
+    target rows against all 65536 sources (computed once)."""
     wl = mmvm_inputs.two_patches()
-    gx, gM = _gpu_rhs(mm, wl, 0.0, mm.MMVM_MIXED_FP32)
-    assert np.all(np.isfinite(gM)) and np.all(np.isfinite(gx))
     rows = np.random.default_rng(2).choice(wl.n, 4, replace=False)
     ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=rows)
+    return wl, rows, ox, oM
+
+
+@pytest.mark.parametrize("variant", [None, 0, 8, 10])
+def test_two_patches_full_size_sampled_rows(mm, two_patches_rows, variant, monkeypatch):
+    """N = 65536, M = 6 two patches (mixed precision), in the launch
+    configurations bench.py times (the autotuner's choice; the fused variant
+    0 and the split variants 8 and 10 forced): sampled rows vs the oracle."""
+    wl, rows, ox, oM = two_patches_rows
+    if variant is not None:
+        monkeypatch.setenv("MMVM_PAIR_VARIANT", str(variant))
+    with mm.Context(wl.order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32) as ctx:
+        ctx.set_state(wl.x, wl.moments, 0.0)
+        cfg = mm.mmvm_pair_config(ctx.handle)
+        gx, gM = ctx.rhs()
+    if variant is not None:
+        assert cfg["variant"] == variant
+    assert np.all(np.isfinite(gM)) and np.all(np.isfinite(gx))
     assert vel_error(gx[rows], ox) <= MIXED_RHS_TOL
+    assert rhs_error(gM[rows], oM, wl.order, wl.lam0) <= MIXED_RHS_TOL
     # total impulse sum_j M00 xdot^j vanishes (pair antisymmetry) at any size
     imp = (wl.moments[:, :1] * gx).sum(0)
     assert np.abs(imp).max() <= 1e-6 * np.abs(wl.moments[:, :1] * gx).sum()
