@@ -223,6 +223,9 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
   const bool use_far = f32 && gdata != nullptr;
   // this thread's target: pairs on each path, tile expansions evaluated
   unsigned n_near = 0, n_far = 0, n_m2p = 0, n_m2p_pairs = 0;
+  // did this warp accumulate anything? (warp-uniform; a warp that did not
+  // stores zeros without touching its sums: FP64 arithmetic is scarce)
+  bool work = false;
   // this warp's 32 targets form one group; a warp wholly past n does no work
   // (but still takes part in every barrier)
   const int wfirst = tile0 + warp * 32;
@@ -247,6 +250,7 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
         const bool m2p = far_tile && tile_takes_m2p<M>(gdata, tgroup, sg);
         const bool far = far_tile && !m2p;  // source by source
         if (m2p) {  // the whole tile through its expansion (warp-uniform, no barrier)
+          work = true;
           constexpr int NA = m2p_terms(M);
           const float* g = group_rec<M>(gdata, sg);
           const float cx = g[4], cy = g[5];
@@ -293,6 +297,7 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
             }
           }
           if (far) {
+            work = true;
             float tmp[NBL];
 #pragma unroll
             for (int b = 0; b < NBL; ++b) tmp[b] = 0.f;
@@ -326,6 +331,7 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
       if constexpr (f32) {
         if (near) flush_sums<LO, HI, PART, TPC>(acc, acc_hi, acc_lo, slot);
       }
+      work = work || near;
     }
   }
   if (LO == 1 && PART != 2 && counts != nullptr) {
@@ -345,10 +351,10 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
     static_for<0, NBL>([&](auto bc) {
       constexpr int b = decltype(bc)::value;
       if constexpr (PC::in(b)) {
-        double v;
+        double v = 0.0;
         if constexpr (f32) {
           constexpr int q = PC::slot(b) * TPC;
-          v = (double)acc_hi[q + slot] + (double)acc_lo[q + slot];
+          if (work) v = (double)acc_hi[q + slot] + (double)acc_lo[q + slot];
         } else {
           v = acc[b];
         }
