@@ -415,6 +415,18 @@ def run_served(args, mm):
     }
 
 
+def coefficient_terms(M: int) -> int:
+    """(k, l, i, q) terms of the single-particle coefficient sums of
+    eq:FinalSingleI/II per right-hand side at order M (every k, l with
+    |k|, |l| <= M): what the literal form evaluates, 9.45e8 at M = 60."""
+    ks = np.array([(n - k2, k2) for n in range(M + 1) for k2 in range(n + 1)])
+    k1, k2 = ks[:, 0][:, None], ks[:, 1][:, None]
+    l1, l2 = ks[:, 0][None, :], ks[:, 1][None, :]
+    n1 = np.where(k1 >= 1, (np.minimum(l1, k1 - 1) + 1) * (np.minimum(l2, k2) + 1), 0)
+    n2 = np.where(k2 >= 1, (np.minimum(l1, k1) + 1) * (np.minimum(l2, k2 - 1) + 1), 0)
+    return int(n1.sum() + n2.sum())
+
+
 def separable_fmas(M: int) -> int:
     """Multiply-adds of one separable single-particle RHS at order M (the
     loop bounds of the CUDA passes: Psi, pass 1 (q), pass 2 (l2), pass 3 (i))."""
@@ -493,6 +505,11 @@ def run_single_high(args, mm):
         "rhs_per_s": n_rhs / secs, "unit": "RHS evaluations/s", "seconds": secs,
         "steps_per_s_per_instance": steps / secs,
         "fmas_per_rhs": fmas,
+        "coefficient_terms_per_rhs": coefficient_terms(60),
+        "coefficient_terms_per_s": coefficient_terms(60) * n_rhs / secs,
+        "coefficient_terms_note": "(k, l, i, q) terms of eq:FinalSingleI/II the literal form "
+                                  "evaluates per RHS; the separable passes do fmas_per_rhs "
+                                  "multiply-adds for them",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                      "frac": achieved / peak64,
                      "peak_note": "of measured: FP64 FMA peak measured in this run"},
