@@ -150,12 +150,12 @@ int mmvm_enable_timing(mmvm_ctx* ctx, int on);
 int mmvm_pair_time(mmvm_ctx* ctx, double* ms, int64_t* count);
 
 /* All-pairs kernel configuration in use for the loaded state: out[0..5] =
- * variant index, order slices (kernels per evaluation), targets per CTA,
- * CTAs per SM of the register budget, per-source barrier (0/1), source
- * chunks.  The variant is
- * chosen by timing every compiled variant on the first state of each size
- * class (environment: MMVM_PAIR_VARIANT=<v> forces one, MMVM_AUTOTUNE=0
- * keeps variant 0).                                                         */
+ * variant index, kernels per evaluation (order slices, or the edge and
+ * Laplacian column parts of a split variant), targets per CTA, CTAs per SM
+ * of the register budget, sources between CTA barriers (0: none), source
+ * chunks.  The variant is chosen by timing every compiled variant on its own
+ * source chunking for the first state of each size class (environment:
+ * MMVM_PAIR_VARIANT=<v> forces one, MMVM_AUTOTUNE=0 keeps variant 0).      */
 int mmvm_pair_config(const mmvm_ctx* ctx, int32_t* out);
 
 /* Cumulative counts of ordered pairs the all-pairs kernel evaluated since the
