@@ -155,6 +155,15 @@ __device__ __forceinline__ bool tile_is_far(const float* __restrict__ gdata, int
   return dx * dx + dy * dy >= x_far(M);
 }
 
+// Is the source centre (z1, z2) (hi parts) beyond x_far(M) of every target
+// in the box tb = (min1, max1, min2, max2)?
+template <int M>
+__device__ __forceinline__ bool point_is_far(const float4 tb, float z1, float z2) {
+  const float dx = fmaxf(0.f, fmaxf(tb.x - z1, z1 - tb.y));
+  const float dy = fmaxf(0.f, fmaxf(tb.z - z2, z2 - tb.w));
+  return dx * dx + dy * dy >= x_far(M);
+}
+
 // May source group sg be summed through its expansion about its centre for
 // every target of group tgroup (radius <= theta x distance from the target
 // box to the centre)?
@@ -308,7 +317,14 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
       }
     }
   }
-  // pass 2: near tiles (every tile when the far field is off)
+  // pass 2: near tiles (every tile when the far field is off).  Within a near
+  // tile, a source beyond x_far(M) of the warp's whole target box takes the
+  // point-vortex path (warp-uniform): parts 0 and 1 add its edge columns,
+  // part 2 has nothing to add.
+  float4 tbox = make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (f32) {
+    if (use_far && warp_valid) tbox = *reinterpret_cast<const float4*>(group_rec<M>(gdata, tgroup));
+  }
 #pragma unroll 1
   for (int t0 = c0; t0 < c1; t0 += S) {
     const int cnt = min(S, c1 - t0);
@@ -316,17 +332,40 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
     if constexpr (f32) {
       if (use_far && warp_valid) near = !tile_is_far<M>(gdata, tgroup, t0 / kGroup);
     }
-    if (near && j < n) n_near += cnt;
     if (__syncthreads_or(near)) {
       load_tile(t0, cnt);
       __syncthreads();
 #pragma unroll 1
       for (int s = 0; s < cnt; ++s) {
-        if (near)
-          near_source<M, T, LO, HI, PART>(tile + s * R, t0 + s, j, tz1, tz2, tl1, tl2, acc);
-        if constexpr (SYNC > 0) {
-              if (s % SYNC == SYNC - 1 || s == cnt - 1) __syncthreads();  // CTA-uniform
+        if (near) {
+          const T* rs = tile + s * R;
+          bool sfar = false;
+          if constexpr (f32) {
+            if (use_far) sfar = point_is_far<M>(tbox, rs[0], rs[1]);
+          }
+          if (!sfar) {
+            near_source<M, T, LO, HI, PART>(rs, t0 + s, j, tz1, tz2, tl1, tl2, acc);
+          } else if constexpr (f32 && PART != 2) {
+            float yr[NY], yi[NY];
+#pragma unroll
+            for (int b = 0; b < NY; ++b) {
+              yr[b] = 0.f;
+              yi[b] = 0.f;
             }
+            far_source<M, LO, HI>(reinterpret_cast<const float*>(rs), tz1, tz2, tl1, tl2, yr,
+                                  yi);
+            fold_far<M, float, LO, HI>(yr, yi, reinterpret_cast<float*>(acc));
+          }
+          if (j < n) {
+            if (sfar)
+              ++n_far;
+            else
+              ++n_near;
+          }
+        }
+        if constexpr (SYNC > 0) {
+          if (s % SYNC == SYNC - 1 || s == cnt - 1) __syncthreads();  // CTA-uniform
+        }
       }
       if constexpr (f32) {
         if (near) flush_sums<LO, HI, PART, TPC>(acc, acc_hi, acc_lo, slot);
