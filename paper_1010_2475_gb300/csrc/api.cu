@@ -18,6 +18,7 @@
 #include <string>
 #include <tuple>
 #include <vector>
+#include <vector>
 
 #include "../../include/mmvm.h"
 #include "common.cuh"
@@ -324,9 +325,37 @@ int enqueue_step(mmvm_ctx* c) {
   return MMVM_OK;
 }
 
+// Time one launch of variant e over the first gy of its `chunks` source
+// chunks on the context's current records (after one untimed launch);
+// *per_pair = milliseconds per pair evaluated.
+static cudaError_t time_pair_variant(mmvm_ctx* c, const mmvm::PairEntry& e, int n, int chunks,
+                                     int gy, cudaEvent_t e0, cudaEvent_t e1, double* per_pair) {
+  const int chunk_len = mmvm::round_up((n + chunks - 1) / chunks, c->S);
+  const void* gb = c->far ? c->gbox.p : nullptr;
+  cudaError_t r = mmvm::pair_launch(e, c->rec.p, n, chunks, c->S, gb, c->partial.p, gy, c->st);
+  if (r == cudaSuccess) r = cudaEventRecord(e0, c->st);
+  if (r == cudaSuccess)
+    r = mmvm::pair_launch(e, c->rec.p, n, chunks, c->S, gb, c->partial.p, gy, c->st);
+  if (r == cudaSuccess) r = cudaEventRecord(e1, c->st);
+  if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+  if (r != cudaSuccess) return r;
+  const double pairs = (double)n * std::min((double)gy * chunk_len, (double)n);
+  *per_pair = ms / pairs;
+  if (const char* vb = std::getenv("MMVM_TUNE_VERBOSE"))
+    if (std::atoi(vb))
+      std::fprintf(stderr, "[mmvm tune] M=%d prec=%d n=%d variant %d (slices=%d TPC=%d MINB=%d "
+                   "SYNC=%d), %d of %d chunks: %.3f ms, %.3e pairs/s\n", c->M, c->cfg.precision,
+                   n, e.variant, e.nslices, e.tpc, e.minb, e.sync, gy, chunks, ms,
+                   pairs / (ms * 1e-3));
+  return cudaSuccess;
+}
+
 // Pick the all-pairs variant for this (order, precision, size class): time
 // each compiled variant on the current records (every target tile against the
-// first kTuneChunks source chunks of the variant's own chunking) and keep the
+// first kTuneChunks source chunks of the variant's own chunking), then time
+// the variants within 10 % of the best on their full launch and keep the
 // fastest per pair.  MMVM_PAIR_VARIANT=<v> forces a variant, MMVM_AUTOTUNE=0
 // keeps variant 0.  Runs outside any stream capture (from set_state).
 int tune_pair(mmvm_ctx* c) {
@@ -359,8 +388,14 @@ int tune_pair(mmvm_ctx* c) {
     cudaEvent_t e0, e1;
     MMVM_CK(cudaEventCreate(&e0));
     MMVM_CK(cudaEventCreate(&e1));
+    // stage 1: every variant on the first kTuneChunks chunks of its own
+    // production chunking (many waves of CTAs, so the tail does not decide)
+    struct Cand {
+      int v, chunks;
+      double per_pair;
+    };
+    std::vector<Cand> cands;
     double best = 1e300;
-    choice = 0;
     for (int v = 0; v < nv; ++v) {
       mmvm::PairEntry e = mmvm::pair_entry(c->M, c->cfg.precision, v);
       if (e.M != c->M) continue;
@@ -370,30 +405,33 @@ int tune_pair(mmvm_ctx* c) {
       }
       const int per_sm = mmvm::pair_occupancy(e, c->S);
       if (per_sm < 1) continue;
-      // the production chunking of this variant, first kTuneChunks chunks
-      // (many waves of CTAs, so the tail does not decide)
       const int chunks = std::max(1, chunks_for(n, e.tpc, per_sm, c->cfg.device, c->S));
-      const int chunk_len = mmvm::round_up((n + chunks - 1) / chunks, c->S);
-      const int gy = std::min(chunks, kTuneChunks);
-      const void* gb = c->far ? c->gbox.p : nullptr;
-      MMVM_CK(mmvm::pair_launch(e, c->rec.p, n, chunks, c->S, gb, c->partial.p, gy, c->st));
-      MMVM_CK(cudaEventRecord(e0, c->st));
-      MMVM_CK(mmvm::pair_launch(e, c->rec.p, n, chunks, c->S, gb, c->partial.p, gy, c->st));
-      MMVM_CK(cudaEventRecord(e1, c->st));
-      MMVM_CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      MMVM_CK(cudaEventElapsedTime(&ms, e0, e1));
-      const double pairs = (double)n * std::min((double)gy * chunk_len, (double)n);
-      const double per_pair = ms / pairs;
-      if (const char* vb = std::getenv("MMVM_TUNE_VERBOSE"))
-        if (std::atoi(vb))
-          std::fprintf(stderr, "[mmvm tune] M=%d prec=%d n=%d variant %d (slices=%d TPC=%d "
-                       "MINB=%d SYNC=%d, %d CTAs/SM): %.3f ms, %.3e pairs/s\n", c->M,
-                       c->cfg.precision, n, v, e.nslices, e.tpc, e.minb, e.sync, per_sm, ms,
-                       pairs / (ms * 1e-3));
-      if (per_pair < best) {
-        best = per_pair;
-        choice = v;
+      double per_pair = 0.0;
+      MMVM_CK(time_pair_variant(c, e, n, chunks, std::min(chunks, kTuneChunks), e0, e1,
+                                &per_pair));
+      cands.push_back({v, chunks, per_pair});
+      best = std::min(best, per_pair);
+    }
+    // stage 2: the variants within 10 % of the best, on their full launch
+    choice = 0;
+    double best_full = 1e300;
+    int close = 0;
+    for (const Cand& k : cands) close += k.per_pair <= 1.1 * best ? 1 : 0;
+    for (const Cand& k : cands) {
+      if (close > 1 && k.per_pair > 1.1 * best) continue;
+      double per_pair = k.per_pair;
+      if (close > 1) {
+        mmvm::PairEntry e = mmvm::pair_entry(c->M, c->cfg.precision, k.v);
+        MMVM_CK(mmvm::pair_prepare(e, c->S));
+        if ((size_t)k.chunks * c->NB * n > c->partial.cap) {
+          MMVM_CK(c->partial.ensure((size_t)k.chunks * c->NB * n));
+          c->drop_graph();
+        }
+        MMVM_CK(time_pair_variant(c, e, n, k.chunks, k.chunks, e0, e1, &per_pair));
+      }
+      if (per_pair < best_full) {
+        best_full = per_pair;
+        choice = k.v;
       }
     }
     cudaEventDestroy(e0);
