@@ -189,6 +189,31 @@ def test_two_patches_full_size_sampled_rows(mm, two_patches_rows, variant, monke
     assert np.abs(imp).max() <= 1e-6 * np.abs(wl.moments[:, :1] * gx).sum()
 
 
+@pytest.mark.parametrize("variant", [0, 8, 10])
+def test_two_patches_ragged_size_every_path(mm, variant, monkeypatch):
+    """N = 5003 (ragged for 32-source groups and 128/256/384-target CTAs), two
+    patches, M = 6, mixed precision, far field on: every path of the pair
+    kernel runs (near sources, far sources inside near tiles, far tiles
+    source by source, tile expansions); sampled rows vs the oracle and the
+    work counts add up to every ordered pair."""
+    wl = mmvm_inputs.two_patches(n=5003, order=6, sigma=0.1, seed=77)
+    rng = np.random.default_rng(7)
+    wl.moments[:, 3:] = rng.normal(size=wl.moments[:, 3:].shape) * 1e-3 * wl.moments[:, :1] \
+        * wl.lam0 ** 2
+    monkeypatch.setenv("MMVM_PAIR_VARIANT", str(variant))
+    with mm.Context(6, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32) as ctx:
+        ctx.set_state(wl.x, wl.moments, 0.0)
+        assert mm.mmvm_pair_config(ctx.handle)["variant"] == variant
+        gx, gM = ctx.rhs()
+        near, far_pp, n_m2p, m2p_pairs = mm.mmvm_pair_work(ctx.handle)
+    assert near > 0 and far_pp > 0 and n_m2p > 0
+    assert near + far_pp + m2p_pairs == wl.n * wl.n
+    rows = np.concatenate([[0, wl.n - 1], np.random.default_rng(8).choice(wl.n, 6, replace=False)])
+    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, 6, wl.lam0, wl.nu, rows=rows)
+    assert vel_error(gx[rows], ox) <= MIXED_RHS_TOL
+    assert rhs_error(gM[rows], oM, 6, wl.lam0) <= MIXED_RHS_TOL
+
+
 def test_error_codes(mm):
     wl = mmvm_inputs.random_disk(n=8, order=2, seed=1)
     with mm.Context(2, wl.lam0, wl.nu, mm.MMVM_FP64) as ctx:
