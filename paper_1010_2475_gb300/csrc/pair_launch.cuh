@@ -257,7 +257,10 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
         const int sg = t0 / kGroup;
         const bool far_tile = warp_valid && tile_is_far<M>(gdata, tgroup, sg);
         const bool m2p = far_tile && tile_takes_m2p<M>(gdata, tgroup, sg);
-        const bool far = far_tile && !m2p;  // source by source
+        // source by source; a tile some warp of the CTA needs as near is
+        // left to pass 2, where this warp sums it while the others do near work
+        const bool anynear = __syncthreads_or(warp_valid && !far_tile);
+        const bool far = far_tile && !m2p && !anynear;
         if (m2p) {  // the whole tile through its expansion (warp-uniform, no barrier)
           work = true;
           constexpr int NA = m2p_terms(M);
@@ -329,19 +332,24 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
   for (int t0 = c0; t0 < c1; t0 += S) {
     const int cnt = min(S, c1 - t0);
     bool near = warp_valid;
+    bool sbs = false;  // far for this warp, summed here source by source (pass 1 left it)
     if constexpr (f32) {
-      if (use_far && warp_valid) near = !tile_is_far<M>(gdata, tgroup, t0 / kGroup);
+      if (use_far && warp_valid) {
+        const int sg = t0 / kGroup;
+        near = !tile_is_far<M>(gdata, tgroup, sg);
+        if constexpr (PART != 2) sbs = !near && !tile_takes_m2p<M>(gdata, tgroup, sg);
+      }
     }
     if (__syncthreads_or(near)) {
       load_tile(t0, cnt);
       __syncthreads();
 #pragma unroll 1
       for (int s = 0; s < cnt; ++s) {
-        if (near) {
+        if (near || sbs) {
           const T* rs = tile + s * R;
-          bool sfar = false;
+          bool sfar = sbs;  // every source of a far tile is far from the warp's box
           if constexpr (f32) {
-            if (use_far) sfar = point_is_far<M>(tbox, rs[0], rs[1]);
+            if (use_far && near) sfar = point_is_far<M>(tbox, rs[0], rs[1]);
           }
           if (!sfar) {
             near_source<M, T, LO, HI, PART>(rs, t0 + s, j, tz1, tz2, tl1, tl2, acc);
@@ -368,9 +376,9 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
         }
       }
       if constexpr (f32) {
-        if (near) flush_sums<LO, HI, PART, TPC>(acc, acc_hi, acc_lo, slot);
+        if (near || sbs) flush_sums<LO, HI, PART, TPC>(acc, acc_hi, acc_lo, slot);
       }
-      work = work || near;
+      work = work || near || sbs;
     }
   }
   if (LO == 1 && PART != 2 && counts != nullptr) {
