@@ -20,8 +20,8 @@ static_assert(MMVM_INST_S < kSpec.nslices, "slice index out of range");
 constexpr int kLO = kSpec.s[MMVM_INST_S].lo;
 constexpr int kHI = kSpec.s[MMVM_INST_S].hi;
 constexpr int kPART = kSpec.s[MMVM_INST_S].part;
-constexpr int kTPC = kSpec.TPC;
-constexpr int kMINB = kSpec.MINB;
+constexpr int kTPC = kSpec.s[MMVM_INST_S].tpc ? kSpec.s[MMVM_INST_S].tpc : kSpec.TPC;
+constexpr int kMINB = kSpec.s[MMVM_INST_S].minb ? kSpec.s[MMVM_INST_S].minb : kSpec.MINB;
 constexpr int kSYNC = kSpec.SYNC;
 static_assert(kTPC % 32 == 0, "targets per CTA must be whole warps");
 #define MMVM_KERNEL pair_kernel<kM, T, kLO, kHI, kPART, kTPC, kMINB, kSYNC>
@@ -67,6 +67,7 @@ SliceEntry MMVM_SLICE(MMVM_INST_M, MMVM_INST_PREC, MMVM_INST_V, MMVM_INST_S)() {
   SliceEntry e;
   e.lo = kLO;
   e.hi = kHI;
+  e.tpc = kTPC;
   e.smem = smem_fn;
   e.prepare = prepare_fn;
   e.launch = launch_fn;

@@ -26,6 +26,8 @@ PairEntry pair_entry(int M, int precision, int v) {
   e.minb = sp.MINB;
   e.sync = sp.SYNC;
   e.nslices = sp.nslices;
+  for (int k = 0; k < e.nslices; ++k)
+    if (e.slices[k].tpc != e.tpc) e.uniform_tpc = false;
   e.rec_len = precision == 1 ? rec_len<float>(M) : rec_len<double>(M);
   e.elem_bytes = precision == 1 ? 4 : 8;
   return e;

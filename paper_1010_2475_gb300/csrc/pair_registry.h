@@ -12,6 +12,7 @@ namespace mmvm {
 // One order slice of a variant (one kernel).
 struct SliceEntry {
   int lo = 0, hi = 0;
+  int tpc = 0;  // targets per CTA of this slice's kernel
   size_t (*smem)(int S) = nullptr;
   cudaError_t (*prepare)(int S) = nullptr;  // set the dynamic shared-memory limit
   cudaError_t (*launch)(const void* rec, int n, int chunk_len, int gy, int S, const void* gbox,
@@ -31,6 +32,7 @@ struct PairEntry {
   int tpc = 0;              // targets per CTA
   int minb = 1;             // CTAs per SM the register budget allows
   int sync = 0;             // barrier after every source
+  bool uniform_tpc = true;  // every slice runs tpc targets per CTA (servable)
   int nslices = 0;
   SliceEntry slices[kMaxSlices];
   int rec_len = 0;          // record length in elements

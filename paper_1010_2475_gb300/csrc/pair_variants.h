@@ -10,16 +10,20 @@
 
 namespace mmvm {
 
-// part: which columns of the orders lo..hi the kernel accumulates.
+// part: which columns of the orders lo..hi the kernel accumulates.  A slice
+// may run its own CTA shape (tpc targets per CTA, minb CTAs per SM); such a
+// variant serves contexts only (the server hands out work items of the
+// variant's TPC targets).
 // 0: all of them; 1: the edge columns beta1 <= 1 (the jet, and the far
 // field); 2: the Laplacian columns beta1 >= 2 (Hermite functions only, near
 // tiles only).  A variant that splits a range lists it once per part.
 struct SliceSpec {
   int lo = 0, hi = 0;
   int part = 0;
+  int tpc = 0, minb = 0;  // CTA shape of this slice (0: the variant's)
 };
 
-constexpr int kMaxVariants = 11;
+constexpr int kMaxVariants = 12;
 constexpr int kMaxSlices = 4;
 
 struct VariantSpec {
@@ -30,7 +34,7 @@ struct VariantSpec {
 
 constexpr int n_variants(int M, int prec) {
   if (prec == 0) return 1;
-  return M <= 3 ? 1 : (M == 7 ? 5 : (M == 6 ? 11 : (M == 8 ? 6 : 8)));
+  return M <= 3 ? 1 : (M == 7 ? 5 : (M == 6 ? 12 : (M == 8 ? 6 : 8)));
 }
 
 constexpr VariantSpec variant_spec(int M, int prec, int v) {
@@ -81,7 +85,8 @@ constexpr VariantSpec variant_spec(int M, int prec, int v) {
            : v == 7 ? VariantSpec{1, {{1, 12}}, 128, 2, 2}
            : v == 8 ? VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 128, 3, 1}
            : v == 9 ? VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 128, 4, 1}
-                     : VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 384, 1, 1};
+           : v == 10 ? VariantSpec{2, {{1, 12, 1}, {1, 12, 2}}, 384, 1, 1}
+                     : VariantSpec{2, {{1, 12, 1}, {1, 12, 2, 128, 3}}, 384, 1, 1};
     case 7:
       return v == 0 ? VariantSpec{2, {{1, 8}, {9, 14}}, 128, 2, 1}
            : v == 1 ? VariantSpec{3, {{1, 7}, {8, 11}, {12, 14}}, 128, 2, 1}

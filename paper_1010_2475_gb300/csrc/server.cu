@@ -487,7 +487,7 @@ cudaError_t tune_batch(const mmvm_server* s, Batch& b) {
     choice = 0;
     for (int v = 0; v < nv; ++v) {
       mmvm::PairEntry pe = mmvm::pair_entry(b.M, s->cfg.precision, v);
-      if (pe.M != b.M) continue;
+      if (pe.M != b.M || !pe.uniform_tpc) continue;  // items are pe.tpc targets wide
       if ((e = mmvm::pair_prepare(pe, kGroup)) != cudaSuccess) return e;
       b.pe = pe;
       bool grown = false;
@@ -524,7 +524,7 @@ cudaError_t tune_batch(const mmvm_server* s, Batch& b) {
   }
   if (choice < 0) choice = 0;
   mmvm::PairEntry pe = mmvm::pair_entry(b.M, s->cfg.precision, choice);
-  if (pe.M != b.M) pe = mmvm::pair_entry(b.M, s->cfg.precision, 0);
+  if (pe.M != b.M || !pe.uniform_tpc) pe = mmvm::pair_entry(b.M, s->cfg.precision, 0);
   if ((e = mmvm::pair_prepare(pe, kGroup)) != cudaSuccess) return e;
   b.pe = pe;
   b.dirty = true;

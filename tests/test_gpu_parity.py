@@ -167,7 +167,7 @@ def two_patches_rows():
     return wl, rows, ox, oM
 
 
-@pytest.mark.parametrize("variant", [None, 0, 8, 10])
+@pytest.mark.parametrize("variant", [None, 0, 8, 10, 11])
 def test_two_patches_full_size_sampled_rows(mm, two_patches_rows, variant, monkeypatch):
     """N = 65536, M = 6 two patches (mixed precision), in the launch
     configurations bench.py times (the autotuner's choice; the fused variant
@@ -189,7 +189,7 @@ def test_two_patches_full_size_sampled_rows(mm, two_patches_rows, variant, monke
     assert np.abs(imp).max() <= 1e-6 * np.abs(wl.moments[:, :1] * gx).sum()
 
 
-@pytest.mark.parametrize("variant", [0, 8, 10])
+@pytest.mark.parametrize("variant", [0, 8, 10, 11])
 def test_two_patches_ragged_size_every_path(mm, variant, monkeypatch):
     """N = 5003 (ragged for 32-source groups and 128/256/384-target CTAs), two
     patches, M = 6, mixed precision, far field on: every path of the pair
@@ -295,7 +295,7 @@ def test_every_kernel_variant(mm, order, monkeypatch):
                                  seed=40 + order)
     ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu)
     seen = set()
-    for v in range(11):
+    for v in range(12):
         monkeypatch.setenv("MMVM_PAIR_VARIANT", str(v))
         ctx = mm.Context(order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32)
         try:
