@@ -534,14 +534,16 @@ KERNEL_SOURCES = ("common.cuh", "pair_kernel.cuh", "pair_launch.cuh", "pair_vari
 
 
 def kernel_source_hash() -> str:
-    """sha256 of the all-pairs kernel's sources (the DRAM traffic recorded by
-    ncu belongs to one version of them)."""
+    """sha256 of the all-pairs kernel's code (the DRAM traffic recorded by ncu
+    belongs to one version of it): the sources with // comments and blank
+    lines dropped, so that editing a comment keeps the record."""
     import hashlib
 
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1010_2475_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1010_2475_gb300", "csrc", f)) as fh:
+            lines = (ln.split("//", 1)[0].rstrip() for ln in fh.read().splitlines())
+            h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()
 
 

@@ -3,20 +3,30 @@
 // sums carried across tiles as (hi, lo) float pairs (TwoSum), and the
 // per-(source chunk, target) result written as FP64.
 //
-// One kernel computes one order slice of the outputs, LO <= |beta| <= HI (a
-// variant launches its slices one after another).  Slicing keeps the fully
-// unrolled per-pair code of each kernel short enough for the instruction
-// cache and needs only jet orders LO .. HI + M in each slice.
-// Other variant parameters (chosen per order by the autotuner):
+// One kernel computes one slice of the outputs: the orders
+// LO <= |beta| <= HI, and of those all columns (PART 0), the edge columns
+// beta1 <= 1 only (PART 1: the jet and the far field), or the Laplacian
+// columns only (PART 2: Hermite functions, near sources only).  A variant
+// launches its slices one after another.  Order slices keep the fully
+// unrolled per-pair code short and need only the jet orders LO .. HI + M;
+// column parts let the two halves of the work run with fewer registers
+// each.  Parameters of a variant or slice, chosen per order by the
+// autotuner:
 //   TPC   targets per CTA (a multiple of 32, so each warp is one group);
 //   MINB  CTAs per SM the register budget must allow;
 //   SYNC  > 0: a CTA barrier after every SYNC sources, which keeps the warps
 //         of a CTA on nearby code so they share instruction-cache lines.
-// FP32 runs two passes over the chunk's source tiles: first the tiles whose
-// bounding box is beyond x_far(M) of the warp's target group (point-vortex
-// multipoles, PairFar), then the others (full jet, PairNear); the two paths
-// never hold registers at the same time.  Every barrier is one instruction
-// executed by the whole CTA.
+// FP32 runs two passes over the chunk's source tiles, deciding near or far
+// per (warp, tile) from the bounding boxes (x_far(M)):
+//   pass 1  far tiles: through the tile's expansion about its centre when it
+//           is far enough, else source by source with the point-vortex
+//           multipoles; a source-by-source tile that another warp of the CTA
+//           needs as near is left to pass 2;
+//   pass 2  tiles some warp needs as near: near sources through the full jet
+//           (PairNear), sources beyond x_far of the warp's whole box and the
+//           tiles pass 1 left through the point-vortex multipoles.
+// The near and far paths never hold registers at the same time, and every
+// barrier is one instruction executed by the whole CTA.
 #pragma once
 
 #include "common.cuh"
@@ -187,9 +197,10 @@ __device__ __forceinline__ bool tile_takes_m2p(const float* __restrict__ gdata, 
 // out: this chunk's block [NB][n] of the partial sums (coalesced FP64
 // stores); only the slice's columns are written.  counts (nullable):
 // cumulative (near pairs, far pairs source by source, tile expansions
-// evaluated, pairs they cover), added by the first slice only.  Called by every thread of the CTA; begins by writing only its
-// own shared-memory slots and reuses the tile only after a barrier, so a
-// persistent CTA may call it for one item after another.
+// evaluated, pairs they cover), added by the slice with LO = 1 that is not
+// the Laplacian part.  Called by every thread of the CTA; begins by writing
+// only its own shared-memory slots and reuses the tile only after a
+// barrier, so a persistent CTA may call it for one item after another.
 template <int M, typename T, int LO, int HI, int PART, int TPC, int SYNC>
 __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n, int tile0, int c0,
                                                int c1, int S, const float* __restrict__ gdata,
