@@ -187,6 +187,38 @@ __device__ __forceinline__ bool tile_takes_m2p(const float* __restrict__ gdata, 
   return c.z * c.z <= kM2PTheta2 * (dx * dx + dy * dy);
 }
 
+// The far group sg summed through its expansion about its centre for this
+// thread's target (centre zeta as hi parts tz, lo parts tl; warp-uniform, no
+// barrier), folded into the edge columns of the thread's (hi, lo) sums.
+template <int M, int LO, int HI, int PART, int TPC>
+__device__ __forceinline__ void m2p_tile(const float* __restrict__ gdata, int sg, float tz1,
+                                         float tz2, float tl1, float tl2, float* acc_hi,
+                                         float* acc_lo, int slot) {
+  constexpr int NA = m2p_terms(M);
+  constexpr int NY = HI - LO + 1;
+  constexpr int NBL = PairNear<M, float, LO, HI>::NBL;
+  const float* g = group_rec<M>(gdata, sg);
+  const float cx = g[4], cy = g[5];
+  // w = target - centre = (hi - centre) + lo, as an exact (hi, lo) pair
+  const float d1 = tz1 - cx, d2 = tz2 - cy;
+  const float b1 = d1 + tl1, b2 = d2 + tl2;
+  const float v1 = b1 - d1, v2 = b2 - d2;
+  const float l1 = (d1 - (b1 - v1)) + (tl1 - v1);
+  const float l2 = (d2 - (b2 - v2)) + (tl2 - v2);
+  float yr[NY], yi[NY];
+#pragma unroll
+  for (int b = 0; b < NY; ++b) {
+    yr[b] = 0.f;
+    yi[b] = 0.f;
+  }
+  FarSums<NA, float, LO, HI>::run(b1, b2, l1, l2, g + 8, yr, yi);
+  float tmp[NBL];
+#pragma unroll
+  for (int b = 0; b < NBL; ++b) tmp[b] = 0.f;
+  fold_far<M, float, LO, HI>(yr, yi, tmp);
+  flush_edge_sums<M, LO, HI, PART, TPC>(tmp, acc_hi, acc_lo, slot);
+}
+
 // The work of one CTA: targets tile0 .. tile0 + TPC - 1 (those below n) of
 // one instance against its sources c0 .. c1 - 1.  rec holds the instance's n
 // records (indices are local to it); gdata: one record per group of kGroup
@@ -268,33 +300,14 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
         const int sg = t0 / kGroup;
         const bool far_tile = warp_valid && tile_is_far<M>(gdata, tgroup, sg);
         const bool m2p = far_tile && tile_takes_m2p<M>(gdata, tgroup, sg);
-        // source by source; a tile some warp of the CTA needs as near is
-        // left to pass 2, where this warp sums it while the others do near work
+        // a tile some warp of the CTA needs as near is left to pass 2, where
+        // this warp sums it (expansion or source by source) while the others
+        // do near work
         const bool anynear = __syncthreads_or(warp_valid && !far_tile);
         const bool far = far_tile && !m2p && !anynear;
-        if (m2p) {  // the whole tile through its expansion (warp-uniform, no barrier)
+        if (m2p && !anynear) {  // left to pass 2 when the CTA loads the tile anyway
           work = true;
-          constexpr int NA = m2p_terms(M);
-          const float* g = group_rec<M>(gdata, sg);
-          const float cx = g[4], cy = g[5];
-          // w = target - centre = (hi - centre) + lo, as an exact (hi, lo) pair
-          const float d1 = tz1 - cx, d2 = tz2 - cy;
-          const float b1 = d1 + tl1, b2 = d2 + tl2;
-          const float v1 = b1 - d1, v2 = b2 - d2;
-          const float l1 = (d1 - (b1 - v1)) + (tl1 - v1);
-          const float l2 = (d2 - (b2 - v2)) + (tl2 - v2);
-          float yr[NY], yi[NY];
-#pragma unroll
-          for (int b = 0; b < NY; ++b) {
-            yr[b] = 0.f;
-            yi[b] = 0.f;
-          }
-          FarSums<NA, float, LO, HI>::run(b1, b2, l1, l2, g + 8, yr, yi);
-          float tmp[NBL];
-#pragma unroll
-          for (int b = 0; b < NBL; ++b) tmp[b] = 0.f;
-          fold_far<M, float, LO, HI>(yr, yi, tmp);
-          flush_edge_sums<M, LO, HI, PART, TPC>(tmp, acc_hi, acc_lo, slot);
+          m2p_tile<M, LO, HI, PART, TPC>(gdata, sg, tz1, tz2, tl1, tl2, acc_hi, acc_lo, slot);
           if (j < n) {
             n_m2p += 1;
             n_m2p_pairs += cnt;
@@ -343,17 +356,34 @@ __device__ __forceinline__ void pair_tile_work(const T* __restrict__ rec, int n,
   for (int t0 = c0; t0 < c1; t0 += S) {
     const int cnt = min(S, c1 - t0);
     bool near = warp_valid;
-    bool sbs = false;  // far for this warp, summed here source by source (pass 1 left it)
+    // far for this warp and left by pass 1: summed here through the group's
+    // expansion (m2p2) or source by source (sbs) while the near warps work
+    bool sbs = false, m2p2 = false;
     if constexpr (f32) {
       if (use_far && warp_valid) {
-        const int sg = t0 / kGroup;
-        near = !tile_is_far<M>(gdata, tgroup, sg);
-        if constexpr (PART != 2) sbs = !near && !tile_takes_m2p<M>(gdata, tgroup, sg);
+        near = !tile_is_far<M>(gdata, tgroup, t0 / kGroup);
+        if constexpr (PART != 2) {
+          if (!near) {
+            m2p2 = tile_takes_m2p<M>(gdata, tgroup, t0 / kGroup);
+            sbs = !m2p2;
+          }
+        }
       }
     }
     if (__syncthreads_or(near)) {
       load_tile(t0, cnt);
       __syncthreads();
+      if constexpr (f32 && PART != 2) {
+        if (m2p2) {
+          work = true;
+          m2p_tile<M, LO, HI, PART, TPC>(gdata, t0 / kGroup, tz1, tz2, tl1, tl2, acc_hi, acc_lo,
+                                         slot);
+          if (j < n) {
+            n_m2p += 1;
+            n_m2p_pairs += cnt;
+          }
+        }
+      }
 #pragma unroll 1
       for (int s = 0; s < cnt; ++s) {
         if (near || sbs) {
