@@ -213,7 +213,7 @@ def oracle_rate(wl, rows: int, seed: int = 0):
 
 def _oracle_rows_child(args):
     """One process of the all-cores oracle timing: its own sample of rows."""
-    n, rows, seed = args
+    n, rows, seed, keep = args
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     from oracle.rhs import rhs_regrouped
 
@@ -223,22 +223,55 @@ def _oracle_rows_child(args):
     rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=rng.choice(wl.n, 1))
     sel = rng.choice(wl.n, rows, replace=False)
     t0 = time.perf_counter()
-    rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=sel)
-    return time.perf_counter() - t0
+    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=sel)
+    secs = time.perf_counter() - t0
+    return (secs, sel, ox, oM) if keep else secs
 
 
-def oracle_rate_all_cores(wl, rows_per_proc: int, procs: int, seed: int = 0):
+def oracle_rate_all_cores(wl, rows_per_proc: int, procs: int, seed: int = 0, keep=False):
     """The oracle as it stands, one single-threaded process per host core, each
     on its own sampled target rows against all sources (rows are
     independent): pair-interactions/s = all rows x n / the slowest process's
-    compute time.  A spawn pool, so no process inherits a CUDA context."""
+    compute time.  A spawn pool, so no process inherits a CUDA context.
+    keep: also return the rows and the oracle's values on them."""
     import multiprocessing as mp
 
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
-        secs = pool.map(_oracle_rows_child,
-                        [(wl.n, rows_per_proc, seed + 7919 * i) for i in range(procs)])
-    return procs * rows_per_proc * wl.n / max(secs), max(secs)
+        res = pool.map(_oracle_rows_child,
+                       [(wl.n, rows_per_proc, seed + 7919 * i, keep) for i in range(procs)])
+    secs = [r[0] for r in res] if keep else res
+    value = procs * rows_per_proc * wl.n / max(secs)
+    if not keep:
+        return value, max(secs)
+    return (value, max(secs), np.concatenate([r[1] for r in res]),
+            np.concatenate([r[2] for r in res]), np.concatenate([r[3] for r in res]))
+
+
+def error_vs_oracle(wl, gx, gM, rows, ox, oM, procs):
+    """Per-particle error of the right-hand side at t = 0 against the oracle:
+    the random rows already evaluated, plus rows aimed at the all-pairs
+    kernel's path switches (evaluated here, untimed)."""
+    from tests.parity_util import (oracle_rows_parallel, rhs_error_rows, switch_rows,
+                                   vel_error_rows)
+
+    kinds = switch_rows(wl.x, wl.moments, wl.order, wl.lam0)
+    srows = np.array(sorted({j for v in kinds.values() for j in v}))
+    sx, sM = oracle_rows_parallel(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, srows, procs)
+    out = {"t": 0.0, "norm": "per particle: weighted moment norm (convergence theorem) and "
+                             "Euclidean velocity norm, relative to the particle's own value "
+                             "floored at 1e-3 of the largest row; max over the rows",
+           "rows_random": int(len(rows)), "rows_at_path_switches": int(len(srows)),
+           "xdot_rel": max(vel_error_rows(gx[rows], ox), vel_error_rows(gx[srows], sx)),
+           "dM_rel_weighted": max(rhs_error_rows(gM[rows], oM, wl.order, wl.lam0),
+                                  rhs_error_rows(gM[srows], sM, wl.order, wl.lam0))}
+    pos = {j: i for i, j in enumerate(srows)}
+    out["by_kind"] = {k: {"rows": len(v),
+                          "xdot_rel": vel_error_rows(gx[v], sx[[pos[j] for j in v]]),
+                          "dM_rel_weighted": rhs_error_rows(gM[v], sM[[pos[j] for j in v]],
+                                                            wl.order, wl.lam0)}
+                      for k, v in kinds.items()}
+    return out
 
 
 def cpu_cores_used() -> int:
@@ -250,11 +283,11 @@ def cpu_cores_used() -> int:
 
 
 def run_reference(args, wl):
-    rows = args.oracle_rows
+    rows = args.ref_rows
     procs = args.oracle_procs or os.cpu_count() or 1
     vals, secs = [], []
     for s in range(args.steps):
-        v, dt = oracle_rate_all_cores(wl, rows, procs, seed=s)
+        v, dt = oracle_rate_all_cores(wl, rows, procs, seed=s)[:2]
         vals.append(v)
         secs.append(dt)
     value = len(vals) * procs * rows * wl.n / sum(secs)
@@ -325,47 +358,99 @@ def _run_stream(mm, reqs, precision, arrivals=None):
     return results, makespan, stats
 
 
+def _lat_stats(lat):
+    lat = np.asarray(lat, dtype=float)
+    if not len(lat):
+        return {"count": 0, "p50_ms": None, "p99_ms": None, "mean_ms": None}
+    return {"count": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+
+
 def run_served(args, mm):
-    """Served-stream measurement (see the module docstring)."""
+    """Served-stream measurement (see the module docstring).
+
+    * saturation: the first --serve-burst requests submitted at t = 0 (the
+      request rate and pair-interactions/s the server sustains);
+    * Poisson arrivals of the whole stream at 0.7x and 1.2x that request
+      rate: latency (submit -> result on the host) percentiles over the
+      requests that completed, apart over the diverged ones (stopped with
+      MMVM_E_NUMERIC at the step where their state left the finite range),
+      and over all;
+    * batching gain: the burst's requests one at a time through contexts
+      (same precision, same steps as served) against the burst's makespan.
+    """
     reqs = _served_requests(args.serve_requests)
     work = [4 * r.workload.n ** 2 * r.workload.steps for r in reqs]
     mixed = mm.MMVM_MIXED_FP32
-    burst, span_b, st_b = _run_stream(mm, reqs, mixed)
+    nb = min(args.serve_burst, len(reqs))
+    # warm-up (untimed): the server's and the contexts' per-order variant
+    # choices are made once per process
+    warm = []
+    for order in sorted({r.workload.order for r in reqs}):
+        w = mmvm_inputs.random_disk(n=256, order=order, steps=2, seed=7 + order)
+        warm.append(mmvm_inputs.Request(len(warm), 0.0, w))
+    _run_stream(mm, warm, mixed)
+    seen = set()
+    for r in reqs[:nb]:
+        w = r.workload
+        key = (w.order, int(math.log2(w.n)))
+        if key not in seen:
+            seen.add(key)
+            with mm.Context(w.order, w.lam0, w.nu, mixed) as c:
+                c.set_state(w.x, w.moments, 0.0)
+    burst, span_b, st_b = _run_stream(mm, reqs[:nb], mixed)
     ok_b = [i for i, r in enumerate(burst) if _ok(r)]
 
-    def done_work(res):  # pair interactions computed (a diverged request stops early)
+    def done_work(res, rr):  # pair interactions computed (a diverged request stops early)
         tot = 0
         for i, r in enumerate(res):
             if r is not None:
                 steps = r[2].get("steps", 0) if isinstance(r[2], dict) else 0
-                tot += 4 * reqs[i].workload.n ** 2 * steps
+                tot += 4 * rr[i].workload.n ** 2 * steps
         return tot
 
-    sat_rate = len(reqs) / span_b
+    sat_rate = nb / span_b
 
     def poisson(factor):
         """The stream's own exponential gaps rescaled to factor x the
-        saturation request rate; latencies of the requests that finished."""
+        saturation request rate."""
         rate = factor * sat_rate
         arrivals = [r.arrival / rate for r in reqs]
         res, span, st = _run_stream(mm, reqs, mixed, arrivals)
         ok = [i for i, r in enumerate(res) if _ok(r)]
-        lat = np.array([res[i][2]["latency_ms"] for i in ok])
-        qms = np.array([res[i][2]["queue_ms"] for i in ok])
         div = [i for i, r in enumerate(res) if r is not None and not _ok(r)
                and "NUMERIC" in r[1]]
-        lat_div = np.array([res[i][2].get("latency_ms", np.nan) for i in div])
-        return {"rate_per_s": rate, "of_saturation": factor, "makespan_s": span,
-                "value": done_work(res) / span, "unit": UNIT, "completed": len(ok),
-                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
-                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
-                "mean_ms": float(lat.mean()) if len(lat) else None,
-                "queue_p50_ms": float(np.percentile(qms, 50)) if len(qms) else None,
-                "max_batch": st["max_batch"], "diverged": len(div),
-                "diverged_p50_ms": float(np.median(lat_div)) if len(lat_div) else None}
+        lat_ok = [res[i][2]["latency_ms"] for i in ok]
+        lat_div = [res[i][2].get("latency_ms", np.nan) for i in div]
+        out = {"rate_per_s": rate, "of_saturation": factor, "makespan_s": span,
+               "value": done_work(res, reqs) / span, "unit": UNIT,
+               "completed": _lat_stats(lat_ok), "diverged": _lat_stats(lat_div),
+               "all_finished": _lat_stats(lat_ok + lat_div),
+               "queue_p50_ms": float(np.percentile([res[i][2]["queue_ms"] for i in ok], 50))
+               if ok else None,
+               "max_batch": st["max_batch"], "errors_other": len(reqs) - len(ok) - len(div)}
+        # flat keys of the completed requests (the served-solve latency)
+        out["p50_ms"] = out["completed"]["p50_ms"]
+        out["p99_ms"] = out["completed"]["p99_ms"]
+        return out
 
     pois_under = poisson(0.7)
     pois_over = poisson(1.2)
+    # batching gain: the burst's requests one at a time through contexts, each
+    # for the steps the server ran for it
+    t0 = time.perf_counter()
+    solo_work = 0
+    for i, r in enumerate(burst):
+        w = reqs[i].workload
+        steps = r[2].get("steps", 0) if r is not None and isinstance(r[2], dict) else 0
+        if steps <= 0:
+            continue
+        with mm.Context(w.order, w.lam0, w.nu, mixed) as c:
+            c.set_state(w.x, w.moments, 0.0)
+            c.step(w.dt, steps)
+            c.get_state()
+        solo_work += 4 * w.n ** 2 * steps
+    solo_s = time.perf_counter() - t0
     # errors of the served mixed results against the plain FP64 form (context API)
     from tests.parity_util import state_error
 
@@ -394,20 +479,24 @@ def run_served(args, mm):
                     "weighted norm), mixed precision with the far field",
         "requests": len(reqs),
         "pair_interactions": float(sum(work)),
-        "pair_interactions_done": float(done_work(burst)),
-        "saturation": {"makespan_s": span_b, "value": done_work(burst) / span_b,
+        "saturation": {"requests": nb, "makespan_s": span_b,
+                       "value": done_work(burst, reqs[:nb]) / span_b,
                        "unit": UNIT, "requests_per_s": sat_rate,
                        "completed": len(ok_b), "max_batch": st_b["max_batch"],
                        "ticks": st_b["ticks"]},
         "poisson": pois_under,
         "poisson_over_saturation": pois_over,
-        "not_finite": [{"request": i, "n": reqs[i].workload.n, "order": reqs[i].workload.order,
-                        "steps_done": burst[i][2].get("steps") if burst[i] else None,
-                        "steps": reqs[i].workload.steps}
-                       for i in range(len(reqs)) if i not in ok_b],
+        "batching_gain": {"requests": nb, "served_makespan_s": span_b,
+                          "one_at_a_time_s": solo_s,
+                          "one_at_a_time_value": solo_work / solo_s if solo_s else None,
+                          "gain": solo_s / span_b,
+                          "note": "the saturation burst's requests run one after another "
+                                  "through mixed-precision contexts (set_state, the steps the "
+                                  "server ran, get_state) against the served makespan"},
         "note": "requests whose state leaves the finite range (the truncated moment ODE of "
                 "dense mixed-sign random disks at M >= 4) stop at that step with "
-                "MMVM_E_NUMERIC; p50/p99 are over the requests that finished",
+                "MMVM_E_NUMERIC; p50_ms/p99_ms are over the requests that completed, the "
+                "diverged ones and all finished requests are listed apart",
         "error_vs_fp64": errs,
         "fp64_same_requests": {"requests": len(sub), "pair_interactions": float(sub_work),
                                "fp64_value": sub_work / span64, "mixed_value": sub_work / span32,
@@ -528,6 +617,153 @@ def run_single_high(args, mm):
     }
 
 
+def _timed_steps(mm, ctx, dt, nsteps, stream):
+    """Device time (ms) of nsteps RK4 steps of a context on `stream`."""
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(dt, nsteps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_precision(args, mm, stream, device):
+    """The precision pattern measured like for like: the same two-patch
+    recipe (N = args.prec_n, M = 6, sigma = 0.1, Re = 2000, dt = 0.05), the
+    same 100 RK4 steps, in (i) the plain FP64 form, (ii) mixed precision with
+    every pair through the full jet (MMVM_FLAG_NO_FAR_FIELD) and (iii) mixed
+    precision with the far field (point-vortex far sources and tile
+    expansions).  (ii)/(i) is the gain of the precision split alone, (iii)/(ii)
+    the gain of the far-field evaluation; errors are per particle against (i)
+    after the 100 steps."""
+    from tests.parity_util import position_error, state_error
+
+    wl = mmvm_inputs.two_patches(n=args.prec_n, order=6, sigma=0.1, Re=2000.0, dt=0.05)
+    steps = args.prec_steps
+    out = {"workload": f"two co-rotating Gaussian patches, N={wl.n}, M=6, sigma=0.1, Re=2000, "
+                       f"{steps} RK4 steps of {wl.dt}", "n": wl.n, "steps": steps}
+    res = {}
+    for name, prec, flags in (("fp64", mm.MMVM_FP64, 0),
+                              ("mixed_no_far_field", mm.MMVM_MIXED_FP32, mm.MMVM_FLAG_NO_FAR_FIELD),
+                              ("mixed", mm.MMVM_MIXED_FP32, 0)):
+        with mm.Context(6, wl.lam0, wl.nu, prec, flags=flags, device=device) as c:
+            mm.mmvm_set_stream(c.handle, stream.cuda_stream)
+            c.set_state(wl.x, wl.moments, 0.0)
+            c.step(wl.dt, 1)  # graph capture, warm-up
+            c.set_state(wl.x, wl.moments, 0.0)
+            w0 = mm.mmvm_pair_work(c.handle)
+            ms = _timed_steps(mm, c, wl.dt, steps, stream)
+            w1 = mm.mmvm_pair_work(c.handle)
+            x, m, t = c.get_state()
+        pairs = 4 * steps * wl.n * wl.n
+        res[name] = (x, m, t)
+        out[name] = {"value": pairs / (ms / 1e3), "unit": UNIT, "ms": ms,
+                     "work": dict(zip(("near_pairs", "far_pairs_source_by_source",
+                                       "tile_expansions", "pairs_in_tile_expansions"),
+                                      [int(b - a) for a, b in zip(w0, w1)]))}
+    x64, m64, t64 = res["fp64"]
+    lam = math.sqrt(wl.lam0 ** 2 + 4 * wl.nu * t64)
+    for name in ("mixed_no_far_field", "mixed"):
+        x, m, t = res[name]
+        out[name]["moments_rel_per_particle_vs_fp64"] = state_error(m, m64, 6, lam)
+        out[name]["centroid_err_in_core_sizes_vs_fp64"] = position_error(x, x64, lam)
+    out["precision_gain"] = out["mixed_no_far_field"]["value"] / out["fp64"]["value"]
+    out["far_field_gain"] = out["mixed"]["value"] / out["mixed_no_far_field"]["value"]
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["note"] = ("precision_gain = (ii)/(i): FP32 jets and contractions against FP64, same "
+                   "all-pairs algorithm; far_field_gain = (iii)/(ii): the point-vortex far field "
+                   "and tile expansions, same precision; errors: max over particles of the "
+                   "weighted moment norm relative to the particle's FP64 moments, and the "
+                   "centroid distance in core sizes")
+    return out
+
+
+def run_single_m10(args, mm, stream):
+    """Single particle, order 10 (66 moments), Lamb-Oseen core + quadrupole
+    eps = 0.1 on (2,0)/(0,2)/(1,1), Re = 1000, 500 FP64 RK4 steps of 0.01:
+    RHS evaluations/s, coefficient terms/s, and (cpu leg) the per-particle
+    error against the oracle's 500-step trajectory."""
+    wl = mmvm_inputs.single_quadrupole(order=10, eps=0.1, sigma0=1.0, Re=1000.0)
+    steps = args.m10_steps
+    with mm.Context(10, wl.lam0, wl.nu, mm.MMVM_FP64) as c:
+        mm.mmvm_set_stream(c.handle, stream.cuda_stream)
+        c.set_state(wl.x, wl.moments, 0.0)
+        c.step(wl.dt, 2)
+        c.set_state(wl.x, wl.moments, 0.0)
+        ms = _timed_steps(mm, c, wl.dt, steps, stream)
+        x, m, t = c.get_state()
+    n_rhs = 4 * steps
+    return {"workload": "one particle, order 10 (66 moments), Lamb-Oseen + quadrupole eps=0.1, "
+                        f"Re=1000, {steps} FP64 RK4 steps of {wl.dt}",
+            "rhs_per_s": n_rhs / (ms / 1e3), "unit": "RHS evaluations/s", "ms": ms,
+            "coefficient_terms_per_rhs": coefficient_terms(10),
+            "coefficient_terms_per_s": coefficient_terms(10) * n_rhs / (ms / 1e3),
+            "_final": (wl, m, t)}
+
+
+def single_m10_error(res):
+    """Error of the order-10 trajectory against the oracle's (cpu leg)."""
+    from oracle.rhs import lam_at, rk4
+    from tests.parity_util import state_error
+
+    wl, m, t = res.pop("_final")
+    steps = round(t / wl.dt)
+    t0 = time.perf_counter()
+    ox, oM, ot = rk4(wl.x, wl.moments, 0.0, wl.dt, steps, 10, wl.lam0, wl.nu)
+    res["oracle_seconds"] = time.perf_counter() - t0
+    res["error_vs_oracle"] = {"steps": steps, "t": ot,
+                              "moments_rel_weighted": state_error(m, oM, 10,
+                                                                  lam_at(ot, wl.lam0, wl.nu))}
+
+
+def run_random_disk(args, mm, stream, device):
+    """The random-disk configuration (N = 4096, M = 4, sigma = 0.5, Re = 500,
+    dt = 0.01, up to 200 RK4 steps) in mixed precision with the far field:
+    throughput over the steps whose state stays finite (checked every 10
+    steps), and the per-particle error against the plain FP64 form over the
+    same steps."""
+    from tests.parity_util import position_error, state_error
+
+    wl = mmvm_inputs.random_disk()
+    steps, chunk = args.disk_steps, 10
+    with mm.Context(wl.order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32, device=device) as c:
+        mm.mmvm_set_stream(c.handle, stream.cuda_stream)
+        c.set_state(wl.x, wl.moments, 0.0)
+        c.step(wl.dt, 1)
+        c.set_state(wl.x, wl.moments, 0.0)
+        done, ms_tot, last = 0, 0.0, None
+        while done < steps:
+            k = min(chunk, steps - done)
+            ms_tot += _timed_steps(mm, c, wl.dt, k, stream)
+            x, m, t = c.get_state()
+            if not (np.isfinite(x).all() and np.isfinite(m).all()):
+                break
+            done += k
+            last = (x, m, t)
+    out = {"workload": f"random disk N={wl.n}, M={wl.order}, R=10, sigma={wl.lam0}, Re=500, "
+                       f"dt={wl.dt}, {steps} RK4 steps (mixed precision, far field on)",
+           "steps_requested": steps, "finite_steps": done,
+           "value": 4 * wl.n * wl.n * done / (ms_tot / 1e3) if done else None, "unit": UNIT}
+    if done:
+        with mm.Context(wl.order, wl.lam0, wl.nu, mm.MMVM_FP64, device=device) as c64:
+            mm.mmvm_set_stream(c64.handle, stream.cuda_stream)
+            c64.set_state(wl.x, wl.moments, 0.0)
+            c64.step(wl.dt, done)
+            x64, m64, t64 = c64.get_state()
+        x, m, t = last
+        lam = math.sqrt(wl.lam0 ** 2 + 4 * wl.nu * t)
+        out["error_vs_fp64"] = {"steps": done, "t": t,
+                                "moments_rel_per_particle": state_error(m, m64, wl.order, lam),
+                                "centroid_err_in_core_sizes": position_error(x, x64, lam)}
+    out["note"] = ("the state of this dense mixed-sign random disk leaves the finite range "
+                   "(the truncated moment ODE cannot follow the straining cores); throughput "
+                   "and error cover the steps before the first non-finite 10-step chunk")
+    return out
+
+
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
 KERNEL_SOURCES = ("common.cuh", "pair_kernel.cuh", "pair_launch.cuh", "pair_variants.h",
                   "pair_inst.cu")
@@ -582,7 +818,6 @@ def run_ours(args, wl, rank, world, local_rank):
     import torch
 
     import paper_1010_2475_gb300 as mm
-    from tests.parity_util import rhs_error, vel_error
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -689,13 +924,37 @@ def run_ours(args, wl, rank, world, local_rank):
         e1.record(stream)
         e1.synchronize()
         rhs32_ms = e0.elapsed_time(e1)
+        cnf = mm.Context(sub.order, sub.lam0, sub.nu, mm.MMVM_MIXED_FP32, device=local_rank,
+                         flags=mm.MMVM_FLAG_NO_FAR_FIELD)
+        mm.mmvm_set_stream(cnf.handle, stream.cuda_stream)
+        cnf.set_state(sub.x, sub.moments, 0.0)
+        cnf.rhs()
+        e0.record(stream)
+        mm.mmvm_rhs_device(cnf.handle, d_dx.data_ptr(), d_dm.data_ptr())
+        e1.record(stream)
+        e1.synchronize()
+        rhsnf_ms = e0.elapsed_time(e1)
         fp64 = {"value": sub.n * sub.n / (rhs_ms / 1e3), "unit": UNIT,
                 "workload": f"first {sub.n} particles of the workload, one right-hand side",
                 "ms_per_rhs": rhs_ms, "pair_kernel_ms": p64_ms,
+                "mixed_no_far_field_same_subset": sub.n * sub.n / (rhsnf_ms / 1e3),
                 "mixed_same_subset": sub.n * sub.n / (rhs32_ms / 1e3),
+                "precision_gain": rhs_ms / rhsnf_ms,
+                "far_field_gain": rhsnf_ms / rhs32_ms,
                 "mixed_over_fp64": rhs_ms / rhs32_ms}
         c64.close()
         c32.close()
+        cnf.close()
+    wall = {}
+    t_sec = time.perf_counter()
+    precision = run_precision(args, mm, stream, local_rank) if args.prec_steps > 0 else None
+    wall["precision"] = time.perf_counter() - t_sec
+    t_sec = time.perf_counter()
+    single_m10 = run_single_m10(args, mm, stream) if args.m10_steps > 0 else None
+    wall["single_m10"] = time.perf_counter() - t_sec
+    t_sec = time.perf_counter()
+    disk = run_random_disk(args, mm, stream, local_rank) if args.disk_steps > 0 else None
+    wall["random_disk"] = time.perf_counter() - t_sec
 
     line = None
     pcfg = mm.mmvm_pair_config(ctx.handle)
@@ -719,6 +978,10 @@ def run_ours(args, wl, rank, world, local_rank):
                         "steps": args.e2e_steps},
                 "gpu_launches": launches,
                 "pair_kernel_config": pcfg,
+                "near_pairs_per_s": world * near_l * 4 * args.steps / (total_ms / 1e3),
+                "pairs_by_path_per_rhs": {"near_full_jet": near_l,
+                                          "far_point_vortex_source_by_source": far_l,
+                                          "far_in_tile_expansions": m2p_pairs_l},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                              "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                              "traffic": recorded_traffic(wl.n, pcfg["variant"], pcfg["chunks"]),
@@ -739,11 +1002,18 @@ def run_ours(args, wl, rank, world, local_rank):
                                           "(mmvm_alu_peak); nominal 152 SMs x 128 lanes x 2 "
                                           "flop x 2.07 GHz = %.1f TFLOP/s" % FP32_PEAK_TFLOPS,
                              "frac_of_nominal": achieved / FP32_PEAK_TFLOPS},
-                "fp64": fp64}
+                "fp64": fp64,
+                "mixed_vs_fp64_100_steps": precision,
+                "single_m10": single_m10,
+                "random_disk_n4096": disk}
         if args.serve_requests > 0:
+            t_sec = time.perf_counter()
             line["served"] = run_served(args, mm)
+            wall["served"] = time.perf_counter() - t_sec
         if args.high_steps > 0:
+            t_sec = time.perf_counter()
             line["single_m60"] = run_single_high(args, mm)
+            wall["single_m60"] = time.perf_counter() - t_sec
         if not args.skip_cpu:
             rate, secs, sel, ox, oM = oracle_rate(wl, args.oracle_rows)
             line["cpu_baseline"] = {
@@ -751,16 +1021,25 @@ def run_ours(args, wl, rank, world, local_rank):
                 "sample": f"{args.oracle_rows} random target rows x all {wl.n} sources, one "
                           f"right-hand side at t=0 ({secs:.1f} s, FP64 numpy oracle)"}
             procs = args.oracle_procs or os.cpu_count() or 1
+            rows_all, ox_all, oM_all = [sel], [ox], [oM]
             if procs > 1:
-                v_all, secs_all = oracle_rate_all_cores(wl, args.oracle_rows, procs, seed=99)
+                v_all, secs_all, rr, ox2, oM2 = oracle_rate_all_cores(wl, args.oracle_rows, procs,
+                                                                     seed=99, keep=True)
+                rows_all.append(rr)
+                ox_all.append(ox2)
+                oM_all.append(oM2)
                 line["cpu_baseline_all_cores"] = {
                     "value": v_all, "unit": UNIT, "cores": procs, "kind": "oracle",
                     "sample": f"{procs} processes x {args.oracle_rows} random target rows x all "
                               f"{wl.n} sources, one right-hand side at t=0 ({secs_all:.1f} s)"}
-            line["error_vs_oracle"] = {
-                "rows": args.oracle_rows, "t": 0.0,
-                "xdot_rel": vel_error(gx0[sel], ox),
-                "dM_rel_weighted": rhs_error(gM0[sel], oM, wl.order, wl.lam0)}
+            line["error_vs_oracle"] = error_vs_oracle(wl, gx0, gM0, np.concatenate(rows_all),
+                                                      np.concatenate(ox_all),
+                                                      np.concatenate(oM_all), procs)
+            if single_m10 is not None:
+                single_m10_error(single_m10)
+        elif single_m10 is not None:
+            single_m10.pop("_final", None)
+        line["section_wall_s"] = wall
     ctx.close()
     if dist:
         dist.destroy_process_group()
@@ -775,13 +1054,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--oracle-rows", type=int, default=2)
+    ap.add_argument("--oracle-rows", type=int, default=4,
+                    help="random target rows per oracle process (one process per host core)")
+    ap.add_argument("--ref-rows", type=int, default=2,
+                    help="random target rows per oracle process per step of --impl reference")
     ap.add_argument("--oracle-procs", type=int, default=0,
                     help="processes of the all-cores oracle timing (0: one per host core)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=24,
+    ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the served stream (0: skip the serving measurement)")
+    ap.add_argument("--serve-burst", type=int, default=60,
+                    help="first requests of the stream submitted at once (saturation, batching "
+                         "gain)")
     ap.add_argument("--serve-check", type=int, default=3,
                     help="smallest served requests re-run in FP64 for their error")
     ap.add_argument("--serve-fp64", type=int, default=4,
@@ -790,6 +1075,14 @@ def main():
                     help="RK4 steps of the order-60 single-particle instances (0: skip)")
     ap.add_argument("--high-rows", type=int, default=8,
                     help="sampled rows of the order-60 RHS checked against the oracle")
+    ap.add_argument("--prec-n", type=int, default=4096,
+                    help="particles of the like-for-like precision comparison")
+    ap.add_argument("--prec-steps", type=int, default=100,
+                    help="RK4 steps of the precision comparison (0: skip)")
+    ap.add_argument("--m10-steps", type=int, default=500,
+                    help="FP64 RK4 steps of the order-10 single particle (0: skip)")
+    ap.add_argument("--disk-steps", type=int, default=200,
+                    help="RK4 steps of the N = 4096 random disk (0: skip)")
     ap.add_argument("--n", type=int, default=65536,
                     help="particles (the benchmark is 65536; smaller only for profiling)")
     args = ap.parse_args()

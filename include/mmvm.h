@@ -47,6 +47,9 @@ extern "C" {
 #define MMVM_E_ZERO_CIRCULATION (-2)  /* some M^j[0,0] == 0 (eq:mass)           */
 #define MMVM_E_UNSUPPORTED (-3)       /* order above the compiled limit         */
 #define MMVM_E_OOM (-4)               /* device allocation failed / over budget */
+/* A served request whose footprint exceeds the server's whole HBM budget is
+ * refused at admission with this same code (mmvm_submit).                   */
+#define MMVM_E_ADMISSION MMVM_E_OOM
 #define MMVM_E_NUMERIC (-5)           /* non-finite value in the state          */
 #define MMVM_E_TIMEOUT (-6)           /* a bounded device wait ran out          */
 #define MMVM_E_DEVICE (-7)            /* CUDA runtime error                     */
@@ -86,8 +89,12 @@ typedef struct mmvm_config {
 
 typedef struct mmvm_ctx mmvm_ctx;
 
-/* Create a context on cfg->device.  *out receives the handle; the caller
- * destroys it with mmvm_destroy.  Errors: INVALID_ARG, UNSUPPORTED, DEVICE.  */
+/* Create a context on cfg->device for one instance of the problem of
+ * Section 2 of the paper: particles of order M sharing the core lambda(t)
+ * with lambda(0) = lambda0 and viscosity nu (eq:phi00; the particle centres
+ * and moments come with mmvm_set_state).  *out receives the handle; the
+ * caller destroys it with mmvm_destroy.  Errors: INVALID_ARG, UNSUPPORTED,
+ * DEVICE.                                                                    */
 int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out);
 
 /* Release every device buffer of the context.  NULL is ignored.             */
@@ -122,7 +129,11 @@ int mmvm_rhs(mmvm_ctx* ctx, double* dxdt, double* dMdt);
 int mmvm_rhs_device(mmvm_ctx* ctx, double* d_dxdt, double* d_dMdt);
 
 /* Advance the state by nsteps classic RK4 steps of size dt, lambda evaluated
- * at the stage times.  Asynchronous on the context stream (the steps are
+ * at the stage times (eq:phi00), each stage one right-hand side of
+ * eq:Final_CrossCoef / eq:xjdot_Final.  Classic RK4 is not from the paper:
+ * it is the fixed-step integrator of the benchmark configurations; the
+ * paper integrates with an adaptive embedded pair (Section 4.3), which is
+ * mmvm_integrate.  Asynchronous on the context stream (the steps are
  * replayed from a CUDA graph); mmvm_get_state or mmvm_synchronize waits.     */
 int mmvm_step(mmvm_ctx* ctx, double dt, int64_t nsteps);
 
@@ -149,13 +160,21 @@ int64_t mmvm_launch_count(const mmvm_ctx* ctx);
 int mmvm_enable_timing(mmvm_ctx* ctx, int on);
 int mmvm_pair_time(mmvm_ctx* ctx, double* ms, int64_t* count);
 
-/* All-pairs kernel configuration in use for the loaded state: out[0..5] =
- * variant index, kernels per evaluation (order slices, or the edge and
- * Laplacian column parts of a split variant), targets per CTA, CTAs per SM
- * of the register budget, sources between CTA barriers (0: none), source
- * chunks.  The variant is chosen by timing every compiled variant on its own
- * source chunking for the first state of each size class (environment:
- * MMVM_PAIR_VARIANT=<v> forces one, MMVM_AUTOTUNE=0 keeps variant 0).      */
+/* All-pairs kernel configuration in use for the loaded state, out[0..7]:
+ *  [0] variant index: 0 .. nv-1 the direct form (source tiles shared by the
+ *      target groups of a CTA), nv .. nv+nl-1 the interaction-list form
+ *      (MMVM_MIXED_FP32 with the far field only: near lists per target
+ *      group, near pairs with all warps of a CTA on one target group, a
+ *      separate far-field kernel);
+ *  [1] kernels per evaluation (order slices or column parts; the list form
+ *      counts its list build and far kernel too);
+ *  [2] targets per CTA (list form: threads per CTA of its first near kernel);
+ *  [3] CTAs per SM;  [4] sources between CTA barriers (0: none);
+ *  [5] source chunks (list form: list segments per target group);
+ *  [6] 1 for the list form, else 0;  [7] source ranges of its far kernel.
+ * The variant is chosen by timing the compiled variants for the first state
+ * of each size class (environment: MMVM_PAIR_VARIANT=<v> forces one,
+ * MMVM_AUTOTUNE=0 keeps variant 0).  out must hold 8 values.              */
 int mmvm_pair_config(const mmvm_ctx* ctx, int32_t* out);
 
 /* Cumulative counts of ordered pairs the all-pairs kernel evaluated since the
@@ -334,6 +353,8 @@ int mmvm_request_footprint(int32_t order, int32_t precision, int64_t n, uint64_t
 
 /* Message for the calling thread's last error ("" if none).                 */
 const char* mmvm_last_error(void);
+/* The same message under the name of the boundary's error-text call.        */
+const char* mmvm_last_error_string(void);
 
 #ifdef __cplusplus
 }

@@ -52,7 +52,8 @@ EXPORTS = (
     "mmvm_create", "mmvm_destroy", "mmvm_set_state", "mmvm_set_state_device",
     "mmvm_get_state", "mmvm_get_state_device", "mmvm_rhs", "mmvm_rhs_device",
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
-    "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_enable_timing",
+    "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_last_error_string",
+    "mmvm_enable_timing",
     "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_counts", "mmvm_pair_work", "mmvm_alu_peak",
     "mmvm_rhs_noalloc", "mmvm_integrate", "mmvm_vorticity", "mmvm_nonaxi_enstrophy", "mmvm_server_create", "mmvm_server_destroy", "mmvm_submit",
     "mmvm_poll", "mmvm_server_stats", "mmvm_request_footprint",
@@ -184,6 +185,8 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_request_footprint.restype = ctypes.c_int
     lib.mmvm_last_error.argtypes = []
     lib.mmvm_last_error.restype = ctypes.c_char_p
+    lib.mmvm_last_error_string.argtypes = []
+    lib.mmvm_last_error_string.restype = ctypes.c_char_p
     _lib_handle = lib
     return lib
 
@@ -346,10 +349,10 @@ def mmvm_pair_counts(h):
 
 def mmvm_pair_config(h) -> dict:
     """Variant of the all-pairs kernel in use (see include/mmvm.h)."""
-    out = (ctypes.c_int32 * 6)()
+    out = (ctypes.c_int32 * 8)()
     _check(load_library().mmvm_pair_config(h, out))
     return dict(zip(("variant", "order_slices", "targets_per_cta", "ctas_per_sm",
-                     "sync", "chunks"), list(out)))
+                     "sync", "chunks", "list_form", "far_ranges"), list(out)))
 
 
 class Context:

@@ -97,6 +97,15 @@ struct mmvm_ctx {
   int order_launches = 0;  // kernels launched by one spatial ordering
   DevBuf<double> e_c, psi0;
   mmvm::PairEntry pe;
+  // interaction-list form of the all-pairs kernels (FP32 with the far field):
+  // near lists (G x G entries, G counts), far-field partials (lfar blocks of
+  // the edge columns), list segments of the near partials, device error flag
+  bool list = false;
+  mmvm::ListEntry le;
+  int lseg = 1, lfar = 1;
+  DevBuf<int2> lent;
+  DevBuf<int> lcnt, errf;
+  DevBuf<double> fpart;
   int S = 32;            // sources per shared-memory tile
   int chunks = 1;        // source chunks of the pair kernel
   int finish_tb = 1;     // targets per finish block
@@ -145,6 +154,33 @@ int chunks_for(int64_t n, int tpc, int per_sm, int device, int S) {
   return (int)ch;
 }
 
+// Shape of the list form for n records: list segments per target group
+// (enough CTAs of the near kernels for ~20 waves) and source ranges of the
+// far kernel (~8 waves of warps, at least 16 source groups per warp).
+void list_shape(const mmvm_ctx* c, const mmvm::ListEntry& e, int64_t n, int* lseg, int* lfar) {
+  int dev_sms = 0;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->cfg.device);
+  dev_sms = std::max(dev_sms, 1);
+  const int64_t G = (n + mmvm::kGroup - 1) / mmvm::kGroup;
+  const int occ = std::max(1, mmvm::list_occupancy(e));
+  int64_t seg = (20 * (int64_t)dev_sms * occ + G - 1) / G;
+  if (const char* f = std::getenv("MMVM_LIST_SEGMENTS")) seg = std::atoi(f);  // measurement override
+  *lseg = (int)std::min<int64_t>(std::max<int64_t>(seg, 1), 16);
+  int focc = 0;
+  if (e.far.far_occupancy(&focc) != cudaSuccess) {
+    cudaGetLastError();
+    focc = 1;
+  }
+  const int64_t warp_slots = (int64_t)dev_sms * std::max(focc, 1) * 4;
+  int64_t far = (8 * warp_slots + G - 1) / G;
+  far = std::min<int64_t>(far, std::max<int64_t>(1, G / 16));
+  if (const char* f = std::getenv("MMVM_FAR_RANGES")) far = std::atoi(f);  // measurement override
+  *lfar = (int)std::min<int64_t>(std::max<int64_t>(far, 1), 64);
+}
+
+// Kernels one all-pairs evaluation launches (without prep and ordering).
+int pair_launches(const mmvm_ctx* c) { return c->list ? 2 + c->le.nslices : c->pe.nslices; }
+
 int choose_chunks(const mmvm_ctx* c, int64_t n) {
   const int per_sm = c->pe.nslices ? mmvm::pair_occupancy(c->pe, c->S) : 1;
   return chunks_for(n, c->pe.tpc, per_sm, c->cfg.device, c->S);
@@ -187,6 +223,13 @@ int ensure_buffers(mmvm_ctx* c, int64_t n) {
     MMVM_CK(grow(c->rec, (size_t)n * c->pe.rec_len * c->pe.elem_bytes));
     MMVM_CK(grow(c->partial, (size_t)std::max(c->chunks, kTuneChunks) * c->NB * n));
     if (c->far) {
+      const size_t G = (size_t)((n + mmvm::kGroup - 1) / mmvm::kGroup);
+      MMVM_CK(grow(c->lent, G * G));
+      MMVM_CK(grow(c->lcnt, G));
+      if (!c->errf.p) {
+        MMVM_CK(c->errf.ensure(1));
+        MMVM_CK(cudaMemset(c->errf.p, 0, sizeof(int)));
+      }
       MMVM_CK(grow(c->perm, (size_t)n));
       MMVM_CK(grow(c->gbox, (size_t)mmvm::gdata_len(c->M) *
                                 ((n + mmvm::kGroup - 1) / mmvm::kGroup)));
@@ -243,14 +286,20 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
                               c->st));
     const int slot = mode == 0 ? 4 : mode - 1;
     if (c->timing) MMVM_CK(cudaEventRecord(c->ev[slot][0], c->st));
-    MMVM_CK(mmvm::pair_launch(c->pe, c->rec.p, n, c->chunks, c->S,
-                              c->far ? c->gbox.p : nullptr, c->partial.p, 0, c->st,
-                              c->counts.p));
+    if (c->list) {
+      MMVM_CK(mmvm::list_launch(c->le, reinterpret_cast<const float*>(c->rec.p), n, c->gbox.p,
+                                c->lent.p, c->lcnt.p, c->lseg, c->partial.p, c->lfar, c->fpart.p,
+                                c->counts.p, c->errf.p, c->st));
+    } else {
+      MMVM_CK(mmvm::pair_launch(c->pe, c->rec.p, n, c->chunks, c->S,
+                                c->far ? c->gbox.p : nullptr, c->partial.p, 0, c->st,
+                                c->counts.p));
+    }
     if (c->timing) {
       MMVM_CK(cudaEventRecord(c->ev[slot][1], c->st));
       c->ev_pending[slot] = true;
     }
-    c->launches += (c->far ? 2 : 1) + c->pe.nslices;
+    c->launches += (c->far ? 2 : 1) + pair_launches(c);
   }
   if (c->high) {  // n == 1: separable self term, dx/dt = 0
     mmvm::SelfHighArgs H;
@@ -284,7 +333,12 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
   A.M = c->M;
   A.K = c->K;
   A.NB = c->NB;
-  A.nchunks = n > 1 ? c->chunks : 0;
+  A.nchunks = n > 1 ? (c->list ? c->lseg : c->chunks) : 0;
+  if (n > 1 && c->list) {
+    A.fpart = c->fpart.p;
+    A.nfar = c->lfar;
+    A.n_edge = c->le.far.n_edge;
+  }
   A.targets_per_block = c->finish_tb;
   A.partial = n > 1 ? c->partial.p : nullptr;
   A.perm = perm;
@@ -352,16 +406,61 @@ static cudaError_t time_pair_variant(mmvm_ctx* c, const mmvm::PairEntry& e, int 
   return cudaSuccess;
 }
 
+// Make the list buffers hold list variant e's shape for n records; the
+// shape goes to *lseg / *lfar.
+static int ensure_list_buffers(mmvm_ctx* c, const mmvm::ListEntry& e, int n, int* lseg,
+                               int* lfar) {
+  list_shape(c, e, n, lseg, lfar);
+  const size_t part = (size_t)*lseg * c->NB * n;
+  const size_t fp = (size_t)*lfar * e.far.n_edge * n;
+  if (part > c->partial.cap || fp > c->fpart.cap || !c->fpart.p) {
+    MMVM_CK(c->partial.ensure(std::max(part, c->partial.cap)));
+    MMVM_CK(c->fpart.ensure(std::max(fp, c->fpart.cap)));
+    c->drop_graph();
+  }
+  return MMVM_OK;
+}
+
+// Time one launch of list variant e on the context's current records (after
+// one untimed launch); *per_pair = milliseconds per pair.
+static int time_list_variant(mmvm_ctx* c, const mmvm::ListEntry& e, int n, cudaEvent_t e0,
+                             cudaEvent_t e1, double* per_pair) {
+  int lseg = 1, lfar = 1;
+  int rc = ensure_list_buffers(c, e, n, &lseg, &lfar);
+  if (rc) return rc;
+  const float* rec = reinterpret_cast<const float*>(c->rec.p);
+  MMVM_CK(mmvm::list_launch(e, rec, n, c->gbox.p, c->lent.p, c->lcnt.p, lseg, c->partial.p, lfar,
+                            c->fpart.p, nullptr, c->errf.p, c->st));
+  MMVM_CK(cudaEventRecord(e0, c->st));
+  MMVM_CK(mmvm::list_launch(e, rec, n, c->gbox.p, c->lent.p, c->lcnt.p, lseg, c->partial.p, lfar,
+                            c->fpart.p, nullptr, c->errf.p, c->st));
+  MMVM_CK(cudaEventRecord(e1, c->st));
+  MMVM_CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  MMVM_CK(cudaEventElapsedTime(&ms, e0, e1));
+  *per_pair = ms / ((double)n * n);
+  if (const char* vb = std::getenv("MMVM_TUNE_VERBOSE"))
+    if (std::atoi(vb))
+      std::fprintf(stderr, "[mmvm tune] M=%d n=%d list variant %d (kernels=%d, segments=%d, far "
+                   "ranges=%d): %.3f ms, %.3e pairs/s\n", c->M, n, e.variant, e.nslices + 2,
+                   lseg, lfar, ms, (double)n * n / (ms * 1e-3));
+  return MMVM_OK;
+}
+
 // Pick the all-pairs variant for this (order, precision, size class): time
-// each compiled variant on the current records (every target tile against the
-// first kTuneChunks source chunks of the variant's own chunking), then time
-// the variants within 10 % of the best on their full launch and keep the
-// fastest per pair.  MMVM_PAIR_VARIANT=<v> forces a variant, MMVM_AUTOTUNE=0
-// keeps variant 0.  Runs outside any stream capture (from set_state).
+// each compiled variant of the direct form on the current records (every
+// target tile against the first kTuneChunks source chunks of the variant's
+// own chunking), then time the variants within 10 % of the best on their
+// full launch, and (FP32 with the far field) every variant of the list form
+// on its full launch, and keep the fastest per pair.  Variant numbers
+// 0 .. nv-1 are the direct form, nv .. nv+nl-1 the list form.
+// MMVM_PAIR_VARIANT=<v> forces a variant, MMVM_AUTOTUNE=0 keeps variant 0.
+// Runs outside any stream capture (from set_state).
 int tune_pair(mmvm_ctx* c) {
   const int n = (int)c->n;
   const int nv = mmvm::pair_variant_count(c->M, c->cfg.precision);
-  if (n <= 1 || nv <= 1) return MMVM_OK;
+  const int nl = c->far ? mmvm::list_variant_count(c->M) : 0;
+  if (n <= 1 || nv + nl <= 1) return MMVM_OK;
   const auto key = std::make_tuple(c->cfg.device, c->M, c->cfg.precision, c->far ? 1 : 0,
                                    ilog2(n));
   int choice = -1;
@@ -418,9 +517,9 @@ int tune_pair(mmvm_ctx* c) {
     int close = 0;
     for (const Cand& k : cands) close += k.per_pair <= 1.1 * best ? 1 : 0;
     for (const Cand& k : cands) {
-      if (close > 1 && k.per_pair > 1.1 * best) continue;
+      if ((close > 1 || nl > 0) && k.per_pair > 1.1 * best) continue;
       double per_pair = k.per_pair;
-      if (close > 1) {
+      if (close > 1 || nl > 0) {
         mmvm::PairEntry e = mmvm::pair_entry(c->M, c->cfg.precision, k.v);
         MMVM_CK(mmvm::pair_prepare(e, c->S));
         if ((size_t)k.chunks * c->NB * n > c->partial.cap) {
@@ -434,11 +533,45 @@ int tune_pair(mmvm_ctx* c) {
         choice = k.v;
       }
     }
+    // the list form, every variant on its full launch
+    for (int v = 0; v < nl; ++v) {
+      mmvm::ListEntry e = mmvm::list_entry(c->M, v);
+      if (e.M != c->M) continue;
+      if (mmvm::list_prepare(e) != cudaSuccess || mmvm::list_occupancy(e) < 1) {
+        cudaGetLastError();
+        continue;
+      }
+      double per_pair = 0.0;
+      int rc = time_list_variant(c, e, n, e0, e1, &per_pair);
+      if (rc) return rc;
+      if (per_pair < best_full) {
+        best_full = per_pair;
+        choice = nv + v;
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = choice;
   }
+  if (choice >= nv) {  // list form
+    if (choice >= nv + nl) return fail(MMVM_E_INVALID_ARG, "MMVM_PAIR_VARIANT out of range");
+    mmvm::ListEntry e = mmvm::list_entry(c->M, choice - nv);
+    if (e.M != c->M) return fail(MMVM_E_INVALID_ARG, "MMVM_PAIR_VARIANT out of range");
+    MMVM_CK(mmvm::list_prepare(e));
+    int lseg = 1, lfar = 1;
+    int rc = ensure_list_buffers(c, e, n, &lseg, &lfar);
+    if (rc) return rc;
+    if (!c->list || e.variant != c->le.variant || lseg != c->lseg || lfar != c->lfar)
+      c->drop_graph();
+    c->le = e;
+    c->list = true;
+    c->lseg = lseg;
+    c->lfar = lfar;
+    return MMVM_OK;
+  }
+  if (c->list) c->drop_graph();
+  c->list = false;
   mmvm::PairEntry e = mmvm::pair_entry(c->M, c->cfg.precision, choice);
   if (e.M != c->M) return fail(MMVM_E_INVALID_ARG, "MMVM_PAIR_VARIANT out of range");
   if (e.variant != c->pe.variant || !c->pe.nslices) {
@@ -453,6 +586,20 @@ int tune_pair(mmvm_ctx* c) {
   }
   if (ch != c->chunks) c->drop_graph();
   c->chunks = ch;
+  return MMVM_OK;
+}
+
+// The device error flag of the list kernels (a bulk copy not completed
+// within the wait limit); call after the context stream is synchronised.
+int check_device_flag(mmvm_ctx* c) {
+  if (!c->errf.p) return MMVM_OK;
+  int h = 0;
+  MMVM_CK(cudaMemcpy(&h, c->errf.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    cudaMemset(c->errf.p, 0, sizeof(int));
+    return fail(MMVM_E_TIMEOUT, "a shared-memory stage of the all-pairs kernel did not arrive "
+                                "within the wait limit; the results of the evaluation are invalid");
+  }
   return MMVM_OK;
 }
 
@@ -475,6 +622,8 @@ int check_host_state(const mmvm_ctx* c, int64_t n, const double* x, const double
 extern "C" {
 
 const char* mmvm_last_error(void) { return g_err.c_str(); }
+
+const char* mmvm_last_error_string(void) { return g_err.c_str(); }
 
 int32_t mmvm_num_moments(int32_t order) { return order < 0 ? 0 : mmvm::n_moments(order); }
 
@@ -577,8 +726,12 @@ void mmvm_destroy(mmvm_ctx* c) {
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
   for (auto* b : {&c->x, &c->m, &c->xs, &c->ms, &c->xsum, &c->msum, &c->rdx, &c->rdm, &c->scal,
-                  &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr, &c->dpts, &c->dval, &c->dring, &c->dk})
+                  &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr, &c->dpts, &c->dval, &c->dring, &c->dk,
+                  &c->fpart})
     b->release();
+  c->lent.release();
+  c->lcnt.release();
+  c->errf.release();
   c->rec.release();
   c->counts.release();
   c->derr.release();
@@ -604,7 +757,7 @@ int mmvm_synchronize(mmvm_ctx* c) {
   if (!c) return fail(MMVM_E_INVALID_ARG, "null context");
   MMVM_CK(cudaSetDevice(c->cfg.device));
   MMVM_CK(cudaStreamSynchronize(c->st));
-  return MMVM_OK;
+  return check_device_flag(c);
 }
 
 static int set_state_common(mmvm_ctx* c, int64_t n, const double* x, const double* mom,
@@ -658,7 +811,7 @@ int mmvm_get_state(mmvm_ctx* c, double* x, double* mom, double* t) {
     MMVM_CK(cudaMemcpyAsync(mom, c->m.p, sizeof(double) * c->K * c->n, cudaMemcpyDeviceToHost, c->st));
   if (t) MMVM_CK(cudaMemcpyAsync(t, c->t_dev(), sizeof(double), cudaMemcpyDeviceToHost, c->st));
   MMVM_CK(cudaStreamSynchronize(c->st));
-  return MMVM_OK;
+  return check_device_flag(c);
 }
 
 int mmvm_get_state_device(mmvm_ctx* c, double* d_x, double* d_mom) {
@@ -690,7 +843,7 @@ int mmvm_rhs(mmvm_ctx* c, double* dx, double* dM) {
   MMVM_CK(cudaMemcpyAsync(dx, c->rdx.p, sizeof(double) * 2 * c->n, cudaMemcpyDeviceToHost, c->st));
   MMVM_CK(cudaMemcpyAsync(dM, c->rdm.p, sizeof(double) * c->K * c->n, cudaMemcpyDeviceToHost, c->st));
   MMVM_CK(cudaStreamSynchronize(c->st));
-  return MMVM_OK;
+  return check_device_flag(c);
 }
 
 int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
@@ -736,7 +889,7 @@ int mmvm_step(mmvm_ctx* c, double dt, int64_t nsteps) {
     c->graph_ok = true;
   }
   const int per_step =
-      (c->n > 1 ? 4 * ((c->far ? 2 : 1) + c->pe.nslices + 1) + (c->far ? c->order_launches : 0)
+      (c->n > 1 ? 4 * ((c->far ? 2 : 1) + pair_launches(c) + 1) + (c->far ? c->order_launches : 0)
                 : (c->high ? 20 : 4)) +
       1;
   for (int64_t s = 0; s < nsteps; ++s) {
@@ -948,12 +1101,25 @@ int mmvm_pair_counts(mmvm_ctx* c, int64_t* near_pairs, int64_t* far_pairs) {
 
 int mmvm_pair_config(const mmvm_ctx* c, int32_t* out) {
   if (!c || !out) return fail(MMVM_E_INVALID_ARG, "null argument");
+  if (c->list) {
+    out[0] = mmvm::pair_variant_count(c->M, c->cfg.precision) + c->le.variant;
+    out[1] = c->le.nslices + 2;
+    out[2] = c->le.slices[0].warps * 32;
+    out[3] = mmvm::list_occupancy(c->le);
+    out[4] = 1;
+    out[5] = c->lseg;
+    out[6] = 1;
+    out[7] = c->lfar;
+    return MMVM_OK;
+  }
   out[0] = c->pe.variant;
   out[1] = c->pe.nslices;
   out[2] = c->pe.tpc;
   out[3] = c->pe.minb;
   out[4] = c->pe.sync;
   out[5] = c->chunks;
+  out[6] = 0;
+  out[7] = 0;
   return MMVM_OK;
 }
 

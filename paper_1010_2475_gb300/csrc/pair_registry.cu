@@ -8,6 +8,8 @@ namespace mmvm {
 
 // the slice entry points of every compiled variant, and fill_slices()
 #include "pair_registry_table.inc"
+// the near-kernel and far-kernel entry points of the list form, and fill_list()
+#include "pair_list_table.inc"
 
 int pair_variant_count(int M, int precision) {
   if (M < 0 || M > 8 || (precision != 0 && precision != 1)) return 0;
@@ -89,6 +91,53 @@ cudaError_t pair_launch_batch(const PairEntry& e, const void* rec, const BatchIn
     if (r != cudaSuccess) return r;
   }
   return cudaSuccess;
+}
+
+int list_variant_count(int M) {
+  if (M < 0 || M > 8) return 0;
+  return n_list_variants(M);
+}
+
+ListEntry list_entry(int M, int v) {
+  ListEntry e;
+  if (v < 0 || v >= list_variant_count(M)) return e;
+  if (!fill_list(M * kMaxListVariants + v, e)) return e;
+  e.M = M;
+  e.variant = v;
+  e.nslices = list_variant_spec(M, v).nslices;
+  return e;
+}
+
+cudaError_t list_prepare(const ListEntry& e) {
+  for (int s = 0; s < e.nslices; ++s) {
+    cudaError_t r = e.slices[s].prepare();
+    if (r != cudaSuccess) return r;
+  }
+  return cudaSuccess;
+}
+
+int list_occupancy(const ListEntry& e) {
+  int best = 1 << 30;
+  for (int s = 0; s < e.nslices; ++s) {
+    int b = 0;
+    if (e.slices[s].occupancy(&b) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    best = std::min(best, b);
+  }
+  return e.nslices ? best : 0;
+}
+
+cudaError_t list_launch(const ListEntry& e, const float* rec, int n, const float* gdata,
+                        int2* ent, int* cnt, int C, double* partial, int S, double* fpart,
+                        unsigned long long* counts, int* err, cudaStream_t st) {
+  const int G = (n + kGroup - 1) / kGroup;
+  cudaError_t r = e.far.build(rec, n, G, gdata, ent, cnt, st);
+  if (r == cudaSuccess) r = e.far.far(rec, n, G, gdata, S, fpart, counts, st);
+  for (int s = 0; s < e.nslices && r == cudaSuccess; ++s)
+    r = e.slices[s].launch(rec, n, G, ent, cnt, C, partial, counts, err, st);
+  return r;
 }
 
 }  // namespace mmvm

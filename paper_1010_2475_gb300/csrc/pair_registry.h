@@ -5,6 +5,7 @@
 #include <stddef.h>
 
 #include "common.cuh"
+#include "pair_list_variants.h"
 #include "pair_variants.h"
 
 namespace mmvm {
@@ -64,5 +65,48 @@ int pair_batch_occupancy(const PairEntry& e, int S);
 cudaError_t pair_launch_batch(const PairEntry& e, const void* rec, const BatchInst* inst,
                               const int4* items, const int* n_items, int* counters, int grid,
                               int S, const void* gbox, double* partial, cudaStream_t st);
+
+// ---------------------------------------------------------------- list form
+// Interaction-list form (pair_list.cuh): one near-pair kernel per slice.
+struct ListSliceEntry {
+  int lo = 0, hi = 0, part = 0;
+  int warps = 0;  // warps per CTA (all on one target group)
+  cudaError_t (*prepare)() = nullptr;  // set the dynamic shared-memory limit
+  // grid (G target groups, C list segments); partial: C blocks [NB][n]
+  cudaError_t (*launch)(const float* rec, int n, int G, const int2* ent, const int* cnt, int C,
+                        double* partial, unsigned long long* counts, int* err,
+                        cudaStream_t st) = nullptr;
+  cudaError_t (*occupancy)(int* blocks_per_sm) = nullptr;
+};
+// The list build and the far kernel of one order.
+struct ListFarEntry {
+  cudaError_t (*build)(const float* rec, int n, int G, const float* gdata, int2* ent, int* cnt,
+                       cudaStream_t st) = nullptr;
+  // grid (target groups / 4, S source ranges); fpart: S blocks [n_edge][n]
+  cudaError_t (*far)(const float* rec, int n, int G, const float* gdata, int S, double* fpart,
+                     unsigned long long* counts, cudaStream_t st) = nullptr;
+  cudaError_t (*far_occupancy)(int* blocks_per_sm) = nullptr;
+  int n_edge = 0;  // edge columns of a far block (2 BMAX)
+};
+struct ListEntry {
+  int M = -1;  // -1: no such variant
+  int variant = 0;
+  int nslices = 0;
+  ListSliceEntry slices[kMaxListSlices];
+  ListFarEntry far;
+};
+
+// Number of compiled list variants of order M (FP32 only).
+int list_variant_count(int M);
+ListEntry list_entry(int M, int v);
+cudaError_t list_prepare(const ListEntry& e);
+// CTAs per SM of the near kernels (the smallest), 0 on error.
+int list_occupancy(const ListEntry& e);
+// The whole list form of one right-hand side: list build, far kernel (S
+// source ranges into fpart), near kernels (C list segments into partial).
+// ent: G x G entries, cnt: G counts (G = groups of kGroup records).
+cudaError_t list_launch(const ListEntry& e, const float* rec, int n, const float* gdata,
+                        int2* ent, int* cnt, int C, double* partial, int S, double* fpart,
+                        unsigned long long* counts, int* err, cudaStream_t st);
 
 }  // namespace mmvm

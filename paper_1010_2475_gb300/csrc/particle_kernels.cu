@@ -211,6 +211,15 @@ __device__ __forceinline__ void finish_block(const FinishArgs& A, int j0, double
     double v = 0.0;
     if (j < A.n && A.partial) {
       for (int ch = 0; ch < A.nchunks; ++ch) v += A.partial[((size_t)ch * NB + b) * A.n + j];
+      if (A.fpart) {  // far field of the list form: edge columns only
+        int bn = 1;
+        while (tri(bn + 1) - 1 <= b) ++bn;
+        const int b1 = bn - (b + 1 - tri(bn));
+        if (b1 <= 1) {
+          const int e = 2 * (bn - 1) + b1;
+          for (int ch = 0; ch < A.nfar; ++ch) v += A.fpart[((size_t)ch * A.n_edge + e) * A.n + j];
+        }
+      }
     }
     psi[idx] = v;
   }

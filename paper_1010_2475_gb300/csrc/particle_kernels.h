@@ -14,6 +14,8 @@ struct FinishArgs {
   int nchunks = 0;                  // number of pair partials (0: single particle)
   int targets_per_block = 1;
   const double* partial = nullptr;  // [nchunks][NB][n] by sorted position
+  const double* fpart = nullptr;    // far-field blocks [nfar][n_edge][n] (list form; nullable):
+  int nfar = 0, n_edge = 0;         // edge column e = 2 (|beta| - 1) + beta1, beta1 <= 1
   const int* perm = nullptr;        // sorted position -> particle (null: identity)
   const double* Min = nullptr;      // stage moments (n x K)
   const int* k_off = nullptr;       // finish tables (tables.h)

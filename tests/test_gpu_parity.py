@@ -10,6 +10,15 @@ Tolerances (derived in the design notes):
   accumulated along the order-n recurrences of the jet, ~2 n u with n <= 3M
   and u = 2^-24, plus the tile sums); 1e-5 relative on moments after 100 RK4
   steps.
+Every multi-particle error is per particle (the weighted norm of the
+convergence theorem, Section 2.1.1, for the moments; the Euclidean norm for
+the centroid velocity), maximum over particles.  FP64 results are held
+relative to each particle's own value (floored at 1e-3 of the largest row);
+mixed results relative to the particle's own rounding scale, the summed
+magnitudes of its pair terms (a particle whose velocity is the small
+difference of large pair terms cannot be evaluated in FP32 to better than
+the rounding of those terms), computed from the oracle's pair jet
+(tests/parity_util.py, cond_errors).
 Sizes span several CTA tiles of targets and sources and end in ragged tails;
 at the full benchmark sizes a sample of target rows is checked against the
 oracle's sum over every source.
@@ -21,8 +30,10 @@ import pytest
 
 import mmvm_inputs
 from oracle.rhs import lam_at, rhs_literal, rhs_regrouped, rk4
-from tests.parity_util import (fp64_tolerance, rhs_error, single_particle_condition,
-                               state_error, vel_error)
+from tests.parity_util import (COND_THETA, cond_errors, fp64_tolerance, oracle_rows_parallel,
+                               position_error, rhs_error, rhs_error_rows,
+                               single_particle_condition, state_error, switch_rows, vel_error,
+                               vel_error_rows)
 
 pytestmark = pytest.mark.gpu
 
@@ -67,11 +78,17 @@ def test_multi_particle_rhs(mm, order, n, prec):
     ox, oM = rhs_regrouped(wl.x, wl.moments, t, order, wl.lam0, wl.nu)
     p = mm.MMVM_FP64 if prec == "fp64" else mm.MMVM_MIXED_FP32
     gx, gM = _gpu_rhs(mm, wl, t, p)
-    tol = FP64_TOL if prec == "fp64" else MIXED_RHS_TOL
     lam = lam_at(t, wl.lam0, wl.nu)
-    assert vel_error(gx, ox) <= tol
-    if order >= 2:
-        assert rhs_error(gM, oM, order, lam) <= tol
+    if prec == "fp64":
+        assert vel_error_rows(gx, ox) <= FP64_TOL
+        if order >= 2:
+            assert rhs_error_rows(gM, oM, order, lam) <= FP64_TOL
+    else:
+        ev, em = cond_errors(gx, gM, ox, oM, wl.x, wl.moments, t, order, wl.lam0, wl.nu,
+                             np.arange(wl.n))
+        assert ev <= MIXED_RHS_TOL
+        if order >= 2:
+            assert em <= MIXED_RHS_TOL
 
 
 def test_literal_form_small(mm):
@@ -79,8 +96,8 @@ def test_literal_form_small(mm):
     wl = mmvm_inputs.random_disk(n=4, order=3, radius=1.5, sigma=0.6, amp=0.05, moment_scale="absolute", seed=5)
     ox, oM = rhs_literal(wl.x, wl.moments, 0.0, 3, wl.lam0, wl.nu)
     gx, gM = _gpu_rhs(mm, wl, 0.0, mm.MMVM_FP64)
-    assert vel_error(gx, ox) <= FP64_TOL
-    assert rhs_error(gM, oM, 3, wl.lam0) <= FP64_TOL
+    assert vel_error_rows(gx, ox) <= FP64_TOL
+    assert rhs_error_rows(gM, oM, 3, wl.lam0) <= FP64_TOL
 
 
 def test_near_coincident_and_far_pairs(mm):
@@ -98,8 +115,8 @@ def test_near_coincident_and_far_pairs(mm):
     with mm.Context(order, lam0, nu, mm.MMVM_FP64) as ctx:
         ctx.set_state(x, mom, t)
         gx, gM = ctx.rhs()
-    assert vel_error(gx, ox) <= FP64_TOL
-    assert rhs_error(gM, oM, order, lam0) <= FP64_TOL
+    assert vel_error_rows(gx, ox) <= FP64_TOL
+    assert rhs_error_rows(gM, oM, order, lam0) <= FP64_TOL
 
 
 def test_rk4_fp64_matches_oracle(mm):
@@ -133,6 +150,37 @@ def test_rk4_mixed_100_steps(mm):
     assert np.abs(gx - ox).max() / lam <= 1e-5
 
 
+def test_mixed_trajectory_every_far_path_100_steps(mm):
+    """The stated mixed-precision target on the benchmark recipe: two
+    co-rotating patches, N = 8192, M = 6, sigma = 0.1, Re = 2000, 100 RK4
+    steps of 0.05, mixed precision with every far path active (far sources
+    of near tiles, far tiles source by source, tile expansions), against the
+    plain FP64 form of the same 100 steps (the FP64 path is held to 1e-12 of
+    the oracle on short trajectories above): <= 1e-5 per particle on the
+    moments (weighted norm) and on the centroids (in core sizes)."""
+    wl = mmvm_inputs.two_patches(n=8192, order=6, sigma=0.1, Re=2000.0, dt=0.05)
+    nsteps = 100
+    with mm.Context(6, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32) as ctx:
+        ctx.set_state(wl.x, wl.moments, 0.0)
+        w0 = mm.mmvm_pair_work(ctx.handle)
+        ctx.step(wl.dt, nsteps)
+        gx, gM, gt = ctx.get_state()
+        near, far_pp, n_m2p, m2p_pairs = [b - a for a, b in zip(w0, mm.mmvm_pair_work(ctx.handle))]
+    assert near > 0 and far_pp > 0 and n_m2p > 0 and m2p_pairs > 0
+    assert near + far_pp + m2p_pairs == 4 * nsteps * wl.n * wl.n
+    with mm.Context(6, wl.lam0, wl.nu, mm.MMVM_FP64) as c64:
+        c64.set_state(wl.x, wl.moments, 0.0)
+        c64.step(wl.dt, nsteps)
+        dx, dM, dt_ = c64.get_state()
+    assert gt == dt_
+    assert np.all(np.isfinite(gM)) and np.all(np.isfinite(dM))
+    lam = lam_at(gt, wl.lam0, wl.nu)
+    # the moments have grown from zero: every order is populated
+    assert np.abs(dM[:, 3:]).max() > 1e-3 * np.abs(dM[:, :1]).max() * lam ** 2
+    assert state_error(gM, dM, 6, lam) <= 1e-5
+    assert position_error(gx, dx, lam) <= 1e-5
+
+
 def test_single_particle_config_steps(mm):
     """Single particle, order 10 (the M=10 quadrupole case), 50 FP64 steps."""
     wl = mmvm_inputs.single_quadrupole(order=10, eps=0.1, sigma0=1.0, Re=1000.0)
@@ -152,27 +200,59 @@ def test_random_disk_full_size_sampled_rows(mm, prec):
     gx, gM = _gpu_rhs(mm, wl, 0.0, p)
     rows = np.random.default_rng(1).choice(wl.n, 12, replace=False)
     ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=rows)
-    tol = FP64_TOL if prec == "fp64" else MIXED_RHS_TOL
-    assert vel_error(gx[rows], ox) <= tol
-    assert rhs_error(gM[rows], oM, wl.order, wl.lam0) <= tol
+    if prec == "fp64":
+        assert vel_error_rows(gx[rows], ox) <= FP64_TOL
+        assert rhs_error_rows(gM[rows], oM, wl.order, wl.lam0) <= FP64_TOL
+    else:
+        ev, em = cond_errors(gx[rows], gM[rows], ox, oM, wl.x, wl.moments, 0.0, wl.order,
+                             wl.lam0, wl.nu, rows)
+        assert ev <= MIXED_RHS_TOL and em <= MIXED_RHS_TOL
 
 
 @pytest.fixture(scope="module")
 def two_patches_rows():
-    """The benchmark workload and the oracle's right-hand side on 4 sampled
-    target rows against all 65536 sources (computed once)."""
+    """The benchmark workload and the oracle's right-hand side on 72 target
+    rows against all 65536 sources (computed once, one oracle process per
+    host core): 32 random rows and 40 rows aimed at the kernel's path
+    switches (groups straddling the near/far threshold x_far(M), groups with
+    source tiles just inside the tile-expansion criterion, the loosest group
+    boxes, the smallest circulations, the last group)."""
     wl = mmvm_inputs.two_patches()
-    rows = np.random.default_rng(2).choice(wl.n, 4, replace=False)
-    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows=rows)
-    return wl, rows, ox, oM
+    kinds = {"random": [int(j) for j in np.random.default_rng(2).choice(wl.n, 32, replace=False)]}
+    kinds.update(switch_rows(wl.x, wl.moments, wl.order, wl.lam0))
+    rows = np.array(sorted({j for v in kinds.values() for j in v}))
+    ox, oM = oracle_rows_parallel(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows)
+    from tests.parity_util import abs_scale_rows
+
+    sx, sM = abs_scale_rows(wl.x, wl.moments, 0.0, wl.order, wl.lam0, wl.nu, rows)
+    return wl, rows, ox, oM, kinds, sx, sM
 
 
-@pytest.mark.parametrize("variant", [None, 0, 8, 10, 11])
+def _check_rows(gx, gM, wl, rows, ox, oM, kinds, sx, sM, tol):
+    """Per-particle errors on the sampled rows (conditioning-aware norm),
+    reported per kind of row."""
+    from tests.parity_util import rhs_error_cond, vel_error_cond
+
+    pos = {j: i for i, j in enumerate(rows)}
+    bad = {}
+    for kind, rr in kinds.items():
+        ii = [pos[j] for j in rr]
+        ev = vel_error_cond(gx[rr], ox[ii], sx[ii])
+        em = rhs_error_cond(gM[rr], oM[ii], sM[ii], wl.order, wl.lam0)
+        if not (ev <= tol and em <= tol):
+            bad[kind] = (ev, em)
+    assert not bad, f"rows above {tol}: {bad}"
+    assert vel_error_cond(gx[rows], ox, sx) <= tol
+    assert rhs_error_cond(gM[rows], oM, sM, wl.order, wl.lam0) <= tol
+
+
+@pytest.mark.parametrize("variant", [None, 0, 8, 10, 11, 12, 13, 14, 15])
 def test_two_patches_full_size_sampled_rows(mm, two_patches_rows, variant, monkeypatch):
     """N = 65536, M = 6 two patches (mixed precision), in the launch
-    configurations bench.py times (the autotuner's choice; the fused variant
-    0 and the split variants 8 and 10 forced): sampled rows vs the oracle."""
-    wl, rows, ox, oM = two_patches_rows
+    configurations bench.py times (the autotuner's choice; the direct form's
+    fused variant 0 and split variants 8, 10, 11 and the list form's
+    variants 12-15 forced): sampled rows vs the oracle."""
+    wl, rows, ox, oM, kinds, sx, sM = two_patches_rows
     if variant is not None:
         monkeypatch.setenv("MMVM_PAIR_VARIANT", str(variant))
     with mm.Context(wl.order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32) as ctx:
@@ -182,14 +262,13 @@ def test_two_patches_full_size_sampled_rows(mm, two_patches_rows, variant, monke
     if variant is not None:
         assert cfg["variant"] == variant
     assert np.all(np.isfinite(gM)) and np.all(np.isfinite(gx))
-    assert vel_error(gx[rows], ox) <= MIXED_RHS_TOL
-    assert rhs_error(gM[rows], oM, wl.order, wl.lam0) <= MIXED_RHS_TOL
+    _check_rows(gx, gM, wl, rows, ox, oM, kinds, sx, sM, MIXED_RHS_TOL)
     # total impulse sum_j M00 xdot^j vanishes (pair antisymmetry) at any size
     imp = (wl.moments[:, :1] * gx).sum(0)
     assert np.abs(imp).max() <= 1e-6 * np.abs(wl.moments[:, :1] * gx).sum()
 
 
-@pytest.mark.parametrize("variant", [0, 8, 10, 11])
+@pytest.mark.parametrize("variant", [0, 8, 10, 11, 12, 13, 14, 15])
 def test_two_patches_ragged_size_every_path(mm, variant, monkeypatch):
     """N = 5003 (ragged for 32-source groups and 128/256/384-target CTAs), two
     patches, M = 6, mixed precision, far field on: every path of the pair
@@ -208,10 +287,13 @@ def test_two_patches_ragged_size_every_path(mm, variant, monkeypatch):
         near, far_pp, n_m2p, m2p_pairs = mm.mmvm_pair_work(ctx.handle)
     assert near > 0 and far_pp > 0 and n_m2p > 0
     assert near + far_pp + m2p_pairs == wl.n * wl.n
-    rows = np.concatenate([[0, wl.n - 1], np.random.default_rng(8).choice(wl.n, 6, replace=False)])
+    picks = switch_rows(wl.x, wl.moments, 6, wl.lam0, per_kind=4)
+    rows = np.array(sorted({0, wl.n - 1, *np.random.default_rng(8).choice(wl.n, 6, replace=False),
+                            *(j for v in picks.values() for j in v)}))
     ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, 6, wl.lam0, wl.nu, rows=rows)
-    assert vel_error(gx[rows], ox) <= MIXED_RHS_TOL
-    assert rhs_error(gM[rows], oM, 6, wl.lam0) <= MIXED_RHS_TOL
+    ev, em = cond_errors(gx[rows], gM[rows], ox, oM, wl.x, wl.moments, 0.0, 6, wl.lam0, wl.nu,
+                         rows)
+    assert ev <= MIXED_RHS_TOL and em <= MIXED_RHS_TOL
 
 
 def test_error_codes(mm):
@@ -245,12 +327,20 @@ def test_far_field_matches_full_jet(mm):
         with mm.Context(6, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32, flags=flags) as ctx:
             ctx.set_state(wl.x, wl.moments, 0.0)
             res[name] = ctx.rhs()
+    # every row, relative to the largest row
     assert vel_error(res["far"][0], res["full"][0]) <= 1e-6
     assert rhs_error(res["far"][1], res["full"][1], 6, wl.lam0) <= 1e-6
-    rows = np.random.default_rng(4).choice(wl.n, 6, replace=False)
-    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, 6, wl.lam0, wl.nu, rows=rows)
-    assert vel_error(res["far"][0][rows], ox) <= MIXED_RHS_TOL
-    assert rhs_error(res["far"][1][rows], oM, 6, wl.lam0) <= MIXED_RHS_TOL
+    # sampled rows, per particle (conditioning-aware): far field vs full jet and vs the oracle
+    picks = switch_rows(wl.x, wl.moments, 6, wl.lam0, per_kind=4)
+    rows = np.array(sorted({*np.random.default_rng(4).choice(wl.n, 16, replace=False),
+                            *(j for v in picks.values() for j in v)}))
+    ev, em = cond_errors(res["far"][0][rows], res["far"][1][rows], res["full"][0][rows],
+                         res["full"][1][rows], wl.x, wl.moments, 0.0, 6, wl.lam0, wl.nu, rows)
+    assert ev <= 2e-6 and em <= 2e-6
+    ox, oM = oracle_rows_parallel(wl.x, wl.moments, 0.0, 6, wl.lam0, wl.nu, rows)
+    ev, em = cond_errors(res["far"][0][rows], res["far"][1][rows], ox, oM, wl.x, wl.moments, 0.0,
+                         6, wl.lam0, wl.nu, rows)
+    assert ev <= MIXED_RHS_TOL and em <= MIXED_RHS_TOL
 
 
 @pytest.mark.parametrize("order,kind", [(0, "patches"), (1, "disk"), (2, "disk"), (4, "disk"),
@@ -278,24 +368,39 @@ def test_tile_expansions_match_full_jet(mm, order, kind):
                 near, far_pp, n_m2p, m2p_pairs = mm.mmvm_pair_work(ctx.handle)
     assert n_m2p > 0 and m2p_pairs > 0 and far_pp > 0 and near > 0
     assert near + far_pp + m2p_pairs == wl.n * (wl.n - 1) + wl.n  # every ordered pair, self included
+    # every row, relative to the largest row
     assert vel_error(res["far"][0], res["full"][0]) <= 2e-6
     if order >= 2:
         assert rhs_error(res["far"][1], res["full"][1], order, wl.lam0) <= 2e-6
-    rows = np.random.default_rng(5).choice(wl.n, 3, replace=False)
-    ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu, rows=rows)
-    assert vel_error(res["far"][0][rows], ox) <= MIXED_RHS_TOL
+    # sampled rows, per particle (conditioning-aware): far field vs full jet and vs the oracle
+    picks = switch_rows(wl.x, wl.moments, order, wl.lam0, per_kind=3)
+    rows = np.array(sorted({*np.random.default_rng(5).choice(wl.n, 8, replace=False),
+                            *(j for v in picks.values() for j in v)}))
+    ev, em = cond_errors(res["far"][0][rows], res["far"][1][rows], res["full"][0][rows],
+                         res["full"][1][rows], wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu, rows)
+    assert ev <= 2e-6
     if order >= 2:
-        assert rhs_error(res["far"][1][rows], oM, order, wl.lam0) <= MIXED_RHS_TOL
+        assert em <= 2e-6
+    ox, oM = oracle_rows_parallel(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu, rows)
+    ev, em = cond_errors(res["far"][0][rows], res["far"][1][rows], ox, oM, wl.x, wl.moments, 0.0,
+                         order, wl.lam0, wl.nu, rows)
+    assert ev <= MIXED_RHS_TOL
+    if order >= 2:
+        assert em <= MIXED_RHS_TOL
 
 
-@pytest.mark.parametrize("order", [4, 5, 6, 7, 8])
+@pytest.mark.parametrize("order", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_every_kernel_variant(mm, order, monkeypatch):
-    """Each compiled all-pairs variant reproduces the oracle (mixed precision)."""
+    """Each compiled all-pairs variant (the direct form and the list form)
+    reproduces the oracle (mixed precision, far field on)."""
     wl = mmvm_inputs.random_disk(n=300, order=order, radius=3.0, sigma=0.45, amp=0.02, moment_scale="absolute",
                                  seed=40 + order)
     ox, oM = rhs_regrouped(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu)
+    from tests.parity_util import abs_scale_rows, rhs_error_cond, vel_error_cond
+
+    sx, sM = abs_scale_rows(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu, np.arange(wl.n))
     seen = set()
-    for v in range(12):
+    for v in range(32):
         monkeypatch.setenv("MMVM_PAIR_VARIANT", str(v))
         ctx = mm.Context(order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32)
         try:
@@ -309,6 +414,7 @@ def test_every_kernel_variant(mm, order, monkeypatch):
         ctx.close()
         assert cfg["variant"] == v
         seen.add(v)
-        assert vel_error(gx, ox) <= MIXED_RHS_TOL, cfg
-        assert rhs_error(gM, oM, order, wl.lam0) <= MIXED_RHS_TOL, cfg
-    assert len(seen) >= 3
+        assert vel_error_cond(gx, ox, sx) <= MIXED_RHS_TOL, cfg
+        if order >= 1:
+            assert rhs_error_cond(gM, oM, sM, order, wl.lam0) <= MIXED_RHS_TOL, cfg
+    assert len(seen) >= 2

@@ -129,3 +129,56 @@ def test_odd_symmetry_and_point_vortex_far_field():
         v = (1j) ** a2 * (-1j / (2 * math.pi)) * (-1) ** n * math.factorial(n) / z ** (n + 1)
         np.testing.assert_allclose(F1[:, idx(a1, a2)], v.real, rtol=1e-12, atol=1e-14 * np.abs(v).max())
         np.testing.assert_allclose(F2[:, idx(a1, a2)], -v.imag, rtol=1e-12, atol=1e-14 * np.abs(v).max())
+
+
+def test_far_branch_equals_explicit_leibniz_loop():
+    """The far branch of the oracle's jet (Toeplitz products of
+    Taylor-normalised arrays) against the two-variable Leibniz rule written
+    out term by term: D^a (V_pv - V_pv E) = D^a V_pv - sum_{b <= a}
+    C(a1, b1) C(a2, b2) D^b V_pv D^{a-b} E, with D^b of the holomorphic
+    V_pv,1 - i V_pv,2 = (-i/2pi)/z equal to i^{b2} (-i/2pi)(-1)^n n!/z^{n+1}
+    (n = |b|) and D^c E a product of Hermite functions."""
+    import math
+
+    from oracle.coefficients import multi_indices
+    from oracle.pair_jet import _far
+
+    P, lam = 8, 0.7
+    c = 2.0 * lam * lam
+    s = np.array([[2.1, 0.4], [-1.3, 2.2], [0.2, -3.5], [4.0, 4.0]])
+
+    def herm(k, y):
+        h = [1.0, 2.0 * y]
+        for j in range(1, k):
+            h.append(2.0 * y * h[j] - 2.0 * j * h[j - 1])
+        return h[k]
+
+    def dE(c1, c2, b1, b2):  # D_1^c1 D_2^c2 exp(-(b1^2 + b2^2)/c)
+        out = 1.0
+        for k, b in ((c1, b1), (c2, b2)):
+            t = b / math.sqrt(c)
+            out *= c ** (-k / 2.0) * (-1.0) ** k * herm(k, t) * math.exp(-t * t)
+        return out
+
+    def dpv(b1, b2, z):  # (D^b V_pv,1, D^b V_pv,2)
+        n = b1 + b2
+        f = (1j) ** b2 * (-1j / (2.0 * math.pi)) * (-1.0) ** n * math.factorial(n) / z ** (n + 1)
+        return f.real, -f.imag
+
+    J1, J2 = _far(s, P, c)
+    mi = multi_indices(P)
+    for p, (s1, s2) in enumerate(s):
+        z = s1 + 1j * s2
+        for col, (a1, a2) in enumerate(mi):
+            v1, v2 = dpv(a1, a2, z)
+            for b1 in range(a1 + 1):
+                for b2 in range(a2 + 1):
+                    w = math.comb(a1, b1) * math.comb(a2, b2) * dE(a1 - b1, a2 - b2, s1, s2)
+                    p1, p2 = dpv(b1, b2, z)
+                    v1 -= w * p1
+                    v2 -= w * p2
+            n = a1 + a2
+            scale = max(abs(J1[p, k]) + abs(J2[p, k]) for k, (q1, q2) in enumerate(mi)
+                        if q1 + q2 == n)
+            assert abs(J1[p, col] - v1) <= 1e-12 * scale
+            assert abs(J2[p, col] - v2) <= 1e-12 * scale
