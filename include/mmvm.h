@@ -177,6 +177,12 @@ int mmvm_pair_time(mmvm_ctx* ctx, double* ms, int64_t* count);
  * MMVM_AUTOTUNE=0 keeps variant 0).  out must hold 8 values.              */
 int mmvm_pair_config(const mmvm_ctx* ctx, int32_t* out);
 
+/* Compiled all-pairs variants of (order, precision): *direct variants of the
+ * direct form (numbers 0 .. *direct-1) and *list variants of the list form
+ * (numbers *direct .. *direct + *list - 1; MMVM_MIXED_FP32 with the far field
+ * only, else 0).  Host-only.  Errors: INVALID_ARG.                          */
+int mmvm_pair_variant_counts(int32_t order, int32_t precision, int32_t* direct, int32_t* list);
+
 /* Cumulative counts of ordered pairs the all-pairs kernel evaluated since the
  * context was created, by path: full jet (near) and point-vortex jet (far,
  * MMVM_MIXED_FP32 only, source by source or through tile expansions).  The

@@ -54,7 +54,8 @@ EXPORTS = (
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
     "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_last_error_string",
     "mmvm_enable_timing",
-    "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_counts", "mmvm_pair_work", "mmvm_alu_peak",
+    "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_variant_counts", "mmvm_pair_counts",
+    "mmvm_pair_work", "mmvm_alu_peak",
     "mmvm_rhs_noalloc", "mmvm_integrate", "mmvm_vorticity", "mmvm_nonaxi_enstrophy", "mmvm_server_create", "mmvm_server_destroy", "mmvm_submit",
     "mmvm_poll", "mmvm_server_stats", "mmvm_request_footprint",
 )
@@ -170,6 +171,10 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_pair_counts.restype = ctypes.c_int
     lib.mmvm_pair_config.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
     lib.mmvm_pair_config.restype = ctypes.c_int
+    lib.mmvm_pair_variant_counts.argtypes = [ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32)]
+    lib.mmvm_pair_variant_counts.restype = ctypes.c_int
     lib.mmvm_server_create.argtypes = [ctypes.POINTER(mmvm_server_config), ctypes.POINTER(P)]
     lib.mmvm_server_create.restype = ctypes.c_int
     lib.mmvm_server_destroy.argtypes = [P]
@@ -353,6 +358,15 @@ def mmvm_pair_config(h) -> dict:
     _check(load_library().mmvm_pair_config(h, out))
     return dict(zip(("variant", "order_slices", "targets_per_cta", "ctas_per_sm",
                      "sync", "chunks", "list_form", "far_ranges"), list(out)))
+
+
+def pair_variant_counts(order: int, precision: int = MMVM_MIXED_FP32):
+    """(direct-form variants, list-form variants) compiled for an order."""
+    a = ctypes.c_int32()
+    b = ctypes.c_int32()
+    _check(load_library().mmvm_pair_variant_counts(order, precision, ctypes.byref(a),
+                                                   ctypes.byref(b)))
+    return a.value, b.value
 
 
 class Context:

@@ -106,6 +106,11 @@ struct mmvm_ctx {
   DevBuf<int2> lent;
   DevBuf<int> lcnt, errf;
   DevBuf<double> fpart;
+  // far field of the list form through the tree over the groups (walked from
+  // the lc-th level, tfar nodes there = far blocks), else the flat far kernel
+  bool tree = false;
+  DevBuf<float> tnodes;
+  int lc = 0, tfar = 1;
   int S = 32;            // sources per shared-memory tile
   int chunks = 1;        // source chunks of the pair kernel
   int finish_tb = 1;     // targets per finish block
@@ -179,7 +184,11 @@ void list_shape(const mmvm_ctx* c, const mmvm::ListEntry& e, int64_t n, int* lse
 }
 
 // Kernels one all-pairs evaluation launches (without prep and ordering).
-int pair_launches(const mmvm_ctx* c) { return c->list ? 2 + c->le.nslices : c->pe.nslices; }
+int pair_launches(const mmvm_ctx* c) {
+  if (!c->list) return c->pe.nslices;
+  const int G = (int)((c->n + mmvm::kGroup - 1) / mmvm::kGroup);
+  return 1 + (c->tree ? mmvm::tree_levels(G) + 1 : 1) + c->le.nslices;
+}
 
 int choose_chunks(const mmvm_ctx* c, int64_t n) {
   const int per_sm = c->pe.nslices ? mmvm::pair_occupancy(c->pe, c->S) : 1;
@@ -193,6 +202,7 @@ constexpr int kTuneChunks = 8;
 // Process-wide autotuning results: (device, M, precision, far, log2 n) -> variant.
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
+std::map<std::tuple<int, int, int, int, int>, int> g_tuned_tree;  // list form: tree far field
 
 int ilog2(int64_t v) {
   int r = 0;
@@ -289,7 +299,8 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
     if (c->list) {
       MMVM_CK(mmvm::list_launch(c->le, reinterpret_cast<const float*>(c->rec.p), n, c->gbox.p,
                                 c->lent.p, c->lcnt.p, c->lseg, c->partial.p, c->lfar, c->fpart.p,
-                                c->counts.p, c->errf.p, c->st));
+                                c->tree ? c->tnodes.p : nullptr, c->lc, c->counts.p, c->errf.p,
+                                c->st));
     } else {
       MMVM_CK(mmvm::pair_launch(c->pe, c->rec.p, n, c->chunks, c->S,
                                 c->far ? c->gbox.p : nullptr, c->partial.p, 0, c->st,
@@ -336,7 +347,7 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
   A.nchunks = n > 1 ? (c->list ? c->lseg : c->chunks) : 0;
   if (n > 1 && c->list) {
     A.fpart = c->fpart.p;
-    A.nfar = c->lfar;
+    A.nfar = c->tree ? c->tfar : c->lfar;
     A.n_edge = c->le.far.n_edge;
   }
   A.targets_per_block = c->finish_tb;
@@ -411,6 +422,12 @@ static cudaError_t time_pair_variant(mmvm_ctx* c, const mmvm::PairEntry& e, int 
 static int ensure_list_buffers(mmvm_ctx* c, const mmvm::ListEntry& e, int n, int* lseg,
                                int* lfar) {
   list_shape(c, e, n, lseg, lfar);
+  const size_t tn = (size_t)mmvm::tree_nodes((n + mmvm::kGroup - 1) / mmvm::kGroup) *
+                    mmvm::gdata_len(c->M);
+  if (tn > c->tnodes.cap || !c->tnodes.p) {
+    MMVM_CK(c->tnodes.ensure(std::max<size_t>(tn, 1)));
+    c->drop_graph();
+  }
   const size_t part = (size_t)*lseg * c->NB * n;
   const size_t fp = (size_t)*lfar * e.far.n_edge * n;
   if (part > c->partial.cap || fp > c->fpart.cap || !c->fpart.p) {
@@ -423,17 +440,20 @@ static int ensure_list_buffers(mmvm_ctx* c, const mmvm::ListEntry& e, int n, int
 
 // Time one launch of list variant e on the context's current records (after
 // one untimed launch); *per_pair = milliseconds per pair.
-static int time_list_variant(mmvm_ctx* c, const mmvm::ListEntry& e, int n, cudaEvent_t e0,
-                             cudaEvent_t e1, double* per_pair) {
+static int time_list_variant(mmvm_ctx* c, const mmvm::ListEntry& e, int n, bool tree,
+                             cudaEvent_t e0, cudaEvent_t e1, double* per_pair) {
   int lseg = 1, lfar = 1;
   int rc = ensure_list_buffers(c, e, n, &lseg, &lfar);
   if (rc) return rc;
   const float* rec = reinterpret_cast<const float*>(c->rec.p);
+  int tfar = 1;
+  const int lc = mmvm::tree_chunk_level((n + mmvm::kGroup - 1) / mmvm::kGroup, lfar, &tfar);
+  float* tr = tree ? c->tnodes.p : nullptr;
   MMVM_CK(mmvm::list_launch(e, rec, n, c->gbox.p, c->lent.p, c->lcnt.p, lseg, c->partial.p, lfar,
-                            c->fpart.p, nullptr, c->errf.p, c->st));
+                            c->fpart.p, tr, lc, nullptr, c->errf.p, c->st));
   MMVM_CK(cudaEventRecord(e0, c->st));
   MMVM_CK(mmvm::list_launch(e, rec, n, c->gbox.p, c->lent.p, c->lcnt.p, lseg, c->partial.p, lfar,
-                            c->fpart.p, nullptr, c->errf.p, c->st));
+                            c->fpart.p, tr, lc, nullptr, c->errf.p, c->st));
   MMVM_CK(cudaEventRecord(e1, c->st));
   MMVM_CK(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -441,9 +461,10 @@ static int time_list_variant(mmvm_ctx* c, const mmvm::ListEntry& e, int n, cudaE
   *per_pair = ms / ((double)n * n);
   if (const char* vb = std::getenv("MMVM_TUNE_VERBOSE"))
     if (std::atoi(vb))
-      std::fprintf(stderr, "[mmvm tune] M=%d n=%d list variant %d (kernels=%d, segments=%d, far "
-                   "ranges=%d): %.3f ms, %.3e pairs/s\n", c->M, n, e.variant, e.nslices + 2,
-                   lseg, lfar, ms, (double)n * n / (ms * 1e-3));
+      std::fprintf(stderr, "[mmvm tune] M=%d n=%d list variant %d (near kernels=%d, segments=%d, "
+                   "far %s, far blocks=%d): %.3f ms, %.3e pairs/s\n", c->M, n, e.variant,
+                   e.nslices, lseg, tree ? "tree" : "flat", tree ? tfar : lfar, ms,
+                   (double)n * n / (ms * 1e-3));
   return MMVM_OK;
 }
 
@@ -463,7 +484,7 @@ int tune_pair(mmvm_ctx* c) {
   if (n <= 1 || nv + nl <= 1) return MMVM_OK;
   const auto key = std::make_tuple(c->cfg.device, c->M, c->cfg.precision, c->far ? 1 : 0,
                                    ilog2(n));
-  int choice = -1;
+  int choice = -1, tree_choice = -1;
   if (const char* f = std::getenv("MMVM_PAIR_VARIANT")) choice = std::atoi(f);
   if (choice < 0) {
     if (const char* a = std::getenv("MMVM_AUTOTUNE"))
@@ -542,18 +563,37 @@ int tune_pair(mmvm_ctx* c) {
         continue;
       }
       double per_pair = 0.0;
-      int rc = time_list_variant(c, e, n, e0, e1, &per_pair);
+      int rc = time_list_variant(c, e, n, false, e0, e1, &per_pair);
       if (rc) return rc;
       if (per_pair < best_full) {
         best_full = per_pair;
         choice = nv + v;
       }
     }
+    // the far field of the best list variant through the tree
+    tree_choice = 0;
+    if (choice >= nv) {
+      mmvm::ListEntry e = mmvm::list_entry(c->M, choice - nv);
+      double per_pair = 0.0;
+      int rc = time_list_variant(c, e, n, true, e0, e1, &per_pair);
+      if (rc) return rc;
+      if (per_pair < best_full) {
+        best_full = per_pair;
+        tree_choice = 1;
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = choice;
+    g_tuned_tree[key] = tree_choice;
   }
+  if (tree_choice < 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_tree.find(key);
+    tree_choice = it != g_tuned_tree.end() ? it->second : 1;
+  }
+  if (const char* f = std::getenv("MMVM_FAR_TREE")) tree_choice = std::atoi(f) != 0;
   if (choice >= nv) {  // list form
     if (choice >= nv + nl) return fail(MMVM_E_INVALID_ARG, "MMVM_PAIR_VARIANT out of range");
     mmvm::ListEntry e = mmvm::list_entry(c->M, choice - nv);
@@ -562,12 +602,18 @@ int tune_pair(mmvm_ctx* c) {
     int lseg = 1, lfar = 1;
     int rc = ensure_list_buffers(c, e, n, &lseg, &lfar);
     if (rc) return rc;
-    if (!c->list || e.variant != c->le.variant || lseg != c->lseg || lfar != c->lfar)
+    int tfar = 1;
+    const int lc = mmvm::tree_chunk_level((n + mmvm::kGroup - 1) / mmvm::kGroup, lfar, &tfar);
+    if (!c->list || e.variant != c->le.variant || lseg != c->lseg || lfar != c->lfar ||
+        c->tree != (tree_choice != 0) || lc != c->lc)
       c->drop_graph();
     c->le = e;
     c->list = true;
     c->lseg = lseg;
     c->lfar = lfar;
+    c->tree = tree_choice != 0;
+    c->lc = lc;
+    c->tfar = tfar;
     return MMVM_OK;
   }
   if (c->list) c->drop_graph();
@@ -729,6 +775,7 @@ void mmvm_destroy(mmvm_ctx* c) {
                   &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr, &c->dpts, &c->dval, &c->dring, &c->dk,
                   &c->fpart})
     b->release();
+  c->tnodes.release();
   c->lent.release();
   c->lcnt.release();
   c->errf.release();
@@ -1099,6 +1146,16 @@ int mmvm_pair_counts(mmvm_ctx* c, int64_t* near_pairs, int64_t* far_pairs) {
   return MMVM_OK;
 }
 
+int mmvm_pair_variant_counts(int32_t order, int32_t precision, int32_t* direct, int32_t* list) {
+  if (!direct || !list) return fail(MMVM_E_INVALID_ARG, "null argument");
+  if (order < 0 || order > MMVM_MAX_ORDER_PAIRS ||
+      (precision != MMVM_FP64 && precision != MMVM_MIXED_FP32))
+    return fail(MMVM_E_INVALID_ARG, "order or precision out of range");
+  *direct = mmvm::pair_variant_count(order, precision);
+  *list = precision == MMVM_MIXED_FP32 ? mmvm::list_variant_count(order) : 0;
+  return MMVM_OK;
+}
+
 int mmvm_pair_config(const mmvm_ctx* c, int32_t* out) {
   if (!c || !out) return fail(MMVM_E_INVALID_ARG, "null argument");
   if (c->list) {
@@ -1108,8 +1165,8 @@ int mmvm_pair_config(const mmvm_ctx* c, int32_t* out) {
     out[3] = mmvm::list_occupancy(c->le);
     out[4] = 1;
     out[5] = c->lseg;
-    out[6] = 1;
-    out[7] = c->lfar;
+    out[6] = c->tree ? 2 : 1;
+    out[7] = c->tree ? c->tfar : c->lfar;
     return MMVM_OK;
   }
   out[0] = c->pe.variant;

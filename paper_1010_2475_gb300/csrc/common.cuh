@@ -114,6 +114,23 @@ constexpr float kM2PTheta2 = 0.01f;  // theta^2
 // Re/Im B_j for j < m2p_terms(M); padded to whole float4s.
 __host__ __device__ constexpr int gdata_len(int M) { return round_up(8 + 2 * m2p_terms(M), 4); }
 
+// Binary tree over G groups of kGroup sorted records (the far field of the
+// list form): level L has ceil(G / 2^L) nodes, node i of level L >= 1 holds
+// nodes 2i and 2i+1 of level L-1, the top level one node; the node records
+// of levels 1.. are stored one level after another.
+__host__ __device__ inline int tree_levels(int G) {
+  int L = 0;
+  while ((G + (1 << L) - 1) >> L > 1) ++L;
+  return L;  // index of the top level (0 if G == 1)
+}
+__host__ __device__ inline int tree_level_nodes(int G, int L) { return (G + (1 << L) - 1) >> L; }
+// Offset (in nodes) of level L >= 1 in the node storage.
+__host__ __device__ inline long long tree_level_offset(int G, int L) {
+  long long off = 0;
+  for (int l = 1; l < L; ++l) off += tree_level_nodes(G, l);
+  return off;
+}
+
 // Compile-time loop: f(std::integral_constant<int, i>) for i in [B, E).
 template <int B, int E, typename F>
 __device__ __forceinline__ void static_for(F&& f) {

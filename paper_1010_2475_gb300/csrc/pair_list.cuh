@@ -176,10 +176,12 @@ constexpr int kNearFlush = 32;
 // w the (k W + w)-th near source of the window.  Each warp brings its own
 // sources into NST record slots of its own, one bulk copy per source issued
 // by its lane 0 NST rounds ahead (completion on the slot's mbarrier), so a
-// warp only ever waits for copies it issued itself.  A CTA barrier ends
-// every round (the warps stay on the same code).  err (set to 1) reports a
-// copy that did not complete within the wait limit.
-template <int M, int LO, int HI, int PART, int W, int MINB, int NST>
+// warp only ever waits for copies it issued itself.  SYNC > 0: a CTA barrier
+// after every SYNC rounds keeps the warps on the same code (shared
+// instruction fetch); SYNC = 0 lets them drift apart within a window (their
+// stalls then overlap less).  err (set to 1) reports a copy that did not
+// complete within the wait limit.
+template <int M, int LO, int HI, int PART, int W, int MINB, int NST, int SYNC>
 __global__ void __launch_bounds__(W * 32, MINB)
     near_pair_kernel(const float* __restrict__ rec, int n, int G, const int2* __restrict__ ent,
                      const int* __restrict__ cnt, int C, double* __restrict__ partial,
@@ -301,7 +303,10 @@ __global__ void __launch_bounds__(W * 32, MINB)
         flush_sums<LO, HI, PART, 32>(acc, my_hi, my_lo, lane);
         since_flush = 0;
       }
-      __syncthreads();  // the round's slots have been read; the warps stay in step
+      if constexpr (SYNC > 0) {
+        if (k % SYNC == SYNC - 1) __syncthreads();  // CTA-uniform: the warps stay in step
+      }
+      __syncwarp();  // every lane has read this round's slot before it is refilled
       if (lane == 0 && k + NST < mine) {
         fence_proxy_async_smem();
         issue(k + NST);
@@ -472,6 +477,248 @@ __global__ void __launch_bounds__(kFarWarps * 32)
   }
   if (j < n) {
     // Psi[beta] += -Re((-i)^{beta1 + |beta|} Y[|beta|]) / (2 pi) (see fold_far), in FP64
+    constexpr double s2pi = 1.0 / (2.0 * 3.14159265358979323846);
+    double* o = fpart + (size_t)blockIdx.y * NE * n + j;
+#pragma unroll
+    for (int nb = 1; nb <= BM; ++nb) {
+      const double yr = (double)yhr[nb - 1] + (double)ylr[nb - 1];
+      const double yi = (double)yhi[nb - 1] + (double)yli[nb - 1];
+#pragma unroll
+      for (int bb1 = 0; bb1 < 2; ++bb1) {
+        const int r = (bb1 + nb) & 3;
+        const double v = r == 0 ? -yr : r == 1 ? -yi : r == 2 ? yr : yi;
+        o[(size_t)(2 * (nb - 1) + bb1) * n] = s2pi * v;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ 4. tree far field
+// A binary tree over the Morton order of the groups: level 0 is the groups
+// themselves (gdata), node i of level L >= 1 holds the groups of nodes 2i and
+// 2i+1 of level L-1, i.e. the consecutive groups [i 2^L, (i+1) 2^L).  A node
+// record has the group-record layout (gdata_len): the union of the children's
+// boxes, the box centre c, a radius bounding |source - c| over its sources
+// (max over the children of |c_child - c| + radius_child), the number of
+// its sources (float, in the slot that groups leave 0), and its expansion
+// about c, obtained from the children's expansions by the exact shift
+//   B_j(c) = sum_{k <= j} B^child_{j-k}(c_child) Delta^k / k!,
+//   Delta = c_child - c
+// (the multipoles of a source at distance delta from c_child sit at delta +
+// Delta from c; truncation at j < m2p_terms(M) drops nothing the child had).
+// A node whose box is beyond x_far(M) of a target group's box and whose
+// radius is at most 0.1 of the distance from that box to its centre is
+// summed through its expansion for every target of the group, as a group
+// is (tile_takes_m2p), so the error bound of the tile expansions holds for
+// every node; the traversal replaces the per-group expansions of far groups
+// by as few node expansions as the criterion allows.
+
+// Node i of a level from its children in the level below (nchild records;
+// counts of level-0 children: min(kGroup, n - kGroup g)).
+template <int M>
+__global__ void tree_level_kernel(const float* __restrict__ child, int nchild, int child_is_group,
+                                  int n, float* __restrict__ node, int nnode) {
+  constexpr int GL = gdata_len(M), NA = m2p_terms(M);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnode) return;
+  const int c0 = 2 * i, c1 = min(2 * i + 1, nchild - 1);
+  const float* a = child + (size_t)c0 * GL;
+  const float* b = child + (size_t)c1 * GL;
+  float4 box = *reinterpret_cast<const float4*>(a);
+  if (c1 != c0) {
+    const float4 bb = *reinterpret_cast<const float4*>(b);
+    box = make_float4(fminf(box.x, bb.x), fmaxf(box.y, bb.y), fminf(box.z, bb.z),
+                      fmaxf(box.w, bb.w));
+  }
+  const float cx = 0.5f * (box.x + box.y), cy = 0.5f * (box.z + box.w);
+  float br[NA], bi[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    br[j] = 0.f;
+    bi[j] = 0.f;
+  }
+  float rad = 0.f, count = 0.f;
+  for (int c = c0; c <= c1; ++c) {
+    const float* r = child + (size_t)c * GL;
+    const float dx = r[4] - cx, dy = r[5] - cy;
+    rad = fmaxf(rad, sqrtf(dx * dx + dy * dy) + r[6]);
+    count += child_is_group ? (float)min(kGroup, n - kGroup * c) : r[7];
+    // B_j += sum_k B^child_{j-k} Delta^k / k!
+    float er = 1.f, ei = 0.f;  // Delta^k / k!
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      if (k > 0) {
+        const float tr = (er * dx - ei * dy) * (1.f / k);
+        ei = (er * dy + ei * dx) * (1.f / k);
+        er = tr;
+      }
+#pragma unroll
+      for (int j = k; j < NA; ++j) {
+        const float cr = r[8 + 2 * (j - k)], ci = r[9 + 2 * (j - k)];
+        br[j] = fmaf(cr, er, fmaf(-ci, ei, br[j]));
+        bi[j] = fmaf(cr, ei, fmaf(ci, er, bi[j]));
+      }
+    }
+  }
+  float* o = node + (size_t)i * GL;
+  *reinterpret_cast<float4*>(o) = box;
+  *reinterpret_cast<float4*>(o + 4) = make_float4(cx, cy, rad, count);
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    o[8 + 2 * j] = br[j];
+    o[9 + 2 * j] = bi[j];
+  }
+}
+
+// Node id on the walk's stack: level << kTreeShift | index (levels <= 25 for
+// n <= 2^30, indices < 2^25).  A depth-first walk holds at most one pending
+// sibling per level, so the stack never exceeds levels + 2 <= 27 entries.
+constexpr int kTreeShift = 26;
+constexpr int kTreeStack = 32;
+
+// One warp: target group tg against the subtree rooted at node blockIdx.y of
+// level Lc (the far-field partial block blockIdx.y); S = nodes of level Lc.
+template <int M>
+__global__ void __launch_bounds__(kFarWarps * 32)
+    far_tree_kernel(const float* __restrict__ rec, int n, int G, const float* __restrict__ gdata,
+                    const float* __restrict__ tree, int Lc, double* __restrict__ fpart,
+                    unsigned long long* __restrict__ counts) {
+  constexpr int R = rec_len<float>(M), K = n_moments(M), HDR = Rec<float>::HDR;
+  constexpr int GL = gdata_len(M), NA = m2p_terms(M), BM = bmax_of(M), NE = n_edge(M);
+  constexpr int NF = 2 * (M + 1);
+  __shared__ int stack_s[kFarWarps][kTreeStack];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int tg = blockIdx.x * kFarWarps + wib;
+  if (tg >= G) return;  // the whole warp (no CTA barrier in this kernel)
+  int* stack = stack_s[wib];
+  const int j = tg * kGroup + lane;
+  float tz1 = 3e15f, tz2 = 3e15f, tl1 = 0.f, tl2 = 0.f;
+  if (j < n) {
+    const float* r = rec + (size_t)j * R;
+    tz1 = r[0];
+    tz2 = r[1];
+    tl1 = r[2];
+    tl2 = r[3];
+  }
+  const float4 tb = *reinterpret_cast<const float4*>(gdata + (size_t)tg * GL);
+  float yhr[BM], yhi[BM], ylr[BM], yli[BM], tyr[BM], tyi[BM];
+#pragma unroll
+  for (int b = 0; b < BM; ++b) {
+    yhr[b] = yhi[b] = ylr[b] = yli[b] = tyr[b] = tyi[b] = 0.f;
+  }
+  auto flush = [&]() {
+#pragma unroll
+    for (int b = 0; b < BM; ++b) {
+      two_sum_into(yhr[b], ylr[b], tyr[b]);
+      two_sum_into(yhi[b], yli[b], tyi[b]);
+      tyr[b] = 0.f;
+      tyi[b] = 0.f;
+    }
+  };
+  auto node_rec = [&](int L, int i) -> const float* {
+    return L == 0 ? gdata + (size_t)i * GL : tree + (size_t)(tree_level_offset(G, L) + i) * GL;
+  };
+  unsigned n_far = 0, n_m2p = 0, n_m2p_pairs = 0;
+  int pending = 0;
+  int sp = 0;
+  if (lane == 0) stack[0] = (Lc << kTreeShift) | blockIdx.y;
+  sp = 1;
+  __syncwarp();
+  while (sp > 0) {
+    const int top = stack[--sp];
+    __syncwarp();
+    const int L = top >> kTreeShift, i = top & ((1 << kTreeShift) - 1);
+    const float* nd = node_rec(L, i);
+    const float4 box = *reinterpret_cast<const float4*>(nd);
+    const float4 cen = *reinterpret_cast<const float4*>(nd + 4);
+    const bool far_box = box_dist2(tb, box) >= x_far(M);
+    if (far_box && takes_m2p(tb, cen)) {
+      // the node (or group) through its expansion about its centre
+      const float d1 = tz1 - cen.x, d2 = tz2 - cen.y;
+      const float b1 = d1 + tl1, b2 = d2 + tl2;
+      const float v1 = b1 - d1, v2 = b2 - d2;
+      const float l1 = (d1 - (b1 - v1)) + (tl1 - v1);
+      const float l2 = (d2 - (b2 - v2)) + (tl2 - v2);
+      FarSums<NA, float, 1, BM>::run(b1, b2, l1, l2, nd + 8, tyr, tyi);
+      if (j < n) {
+        n_m2p += 1;
+        n_m2p_pairs += L == 0 ? min(kGroup, n - kGroup * i) : (unsigned)cen.w;
+      }
+      if (++pending == kFarFlush) {
+        flush();
+        pending = 0;
+      }
+      continue;
+    }
+    if (L > 0) {  // open the node: children 2i (taken first) and 2i+1 (if any)
+      const bool two = 2 * i + 1 < tree_level_nodes(G, L - 1);
+      if (lane == 0) {
+        if (two) stack[sp] = ((L - 1) << kTreeShift) | (2 * i + 1);
+        stack[sp + (two ? 1 : 0)] = ((L - 1) << kTreeShift) | (2 * i);
+      }
+      sp += two ? 2 : 1;
+      __syncwarp();
+      continue;
+    }
+    // a group not summed through its expansion: source by source, every
+    // source of a far group or the sources of a near group that lie beyond
+    // x_far(M) of the whole target box
+    const int g = i;
+    const int nsrc = min(kGroup, n - g * kGroup);
+    const int s = g * kGroup + lane;
+    float z[4] = {0.f, 0.f, 0.f, 0.f}, af[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) af[q] = 0.f;
+    bool mine = false;
+    if (lane < nsrc) {
+      const float* r = rec + (size_t)s * R;
+      const float4 zz = *reinterpret_cast<const float4*>(r);
+      z[0] = zz.x;
+      z[1] = zz.y;
+      z[2] = zz.z;
+      z[3] = zz.w;
+      mine = far_box || point_is_far<M>(tb, zz.x, zz.y);
+      if (mine) {
+#pragma unroll
+        for (int q = 0; q < NF; ++q) af[q] = r[HDR + K + q];
+      }
+    }
+    unsigned fm = __ballot_sync(0xffffffffu, mine);
+    if (!fm) continue;
+    if (j < n) n_far += __popc(fm);
+    while (fm) {
+      const int src = __ffs(fm) - 1;
+      fm &= fm - 1;
+      float a[NF];
+#pragma unroll
+      for (int q = 0; q < NF; ++q) a[q] = __shfl_sync(0xffffffffu, af[q], src);
+      const float sz1 = __shfl_sync(0xffffffffu, z[0], src);
+      const float sz2 = __shfl_sync(0xffffffffu, z[1], src);
+      const float sl1 = __shfl_sync(0xffffffffu, z[2], src);
+      const float sl2 = __shfl_sync(0xffffffffu, z[3], src);
+      const float d1 = tz1 - sz1, e1 = tl1 - sl1;
+      const float d2 = tz2 - sz2, e2 = tl2 - sl2;
+      const float b1 = d1 + e1, b2 = d2 + e2;
+      const float v1 = b1 - d1, v2 = b2 - d2;
+      const float l1 = (d1 - (b1 - v1)) + (e1 - v1);
+      const float l2 = (d2 - (b2 - v2)) + (e2 - v2);
+      FarSums<M + 1, float, 1, BM>::run(b1, b2, l1, l2, a, tyr, tyi);
+    }
+    flush();
+    pending = 0;
+  }
+  flush();
+  if (counts != nullptr) {
+    const unsigned wf = __reduce_add_sync(0xffffffffu, n_far);
+    const unsigned we = __reduce_add_sync(0xffffffffu, n_m2p);
+    const unsigned wp = __reduce_add_sync(0xffffffffu, n_m2p_pairs);
+    if (lane == 0) {
+      if (wf) atomicAdd(counts + 1, (unsigned long long)wf);
+      if (we) atomicAdd(counts + 2, (unsigned long long)we);
+      if (wp) atomicAdd(counts + 3, (unsigned long long)wp);
+    }
+  }
+  if (j < n) {
     constexpr double s2pi = 1.0 / (2.0 * 3.14159265358979323846);
     double* o = fpart + (size_t)blockIdx.y * NE * n + j;
 #pragma unroll

@@ -32,6 +32,25 @@ cudaError_t far_occ_fn(int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, far_pair_kernel<kM>,
                                                        kFarWarps * 32, 0);
 }
+cudaError_t tree_build_fn(const float* gdata, int n, int G, float* tree, cudaStream_t st) {
+  const int top = tree_levels(G);
+  for (int L = 1; L <= top; ++L) {
+    const float* child = L == 1 ? gdata : tree + (size_t)tree_level_offset(G, L - 1) * gdata_len(kM);
+    const int nchild = tree_level_nodes(G, L - 1), nnode = tree_level_nodes(G, L);
+    tree_level_kernel<kM><<<(nnode + 127) / 128, 128, 0, st>>>(
+        child, nchild, L == 1 ? 1 : 0, n, tree + (size_t)tree_level_offset(G, L) * gdata_len(kM),
+        nnode);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+cudaError_t far_tree_fn(const float* rec, int n, int G, const float* gdata, const float* tree,
+                        int Lc, double* fpart, unsigned long long* counts, cudaStream_t st) {
+  dim3 grid((G + kFarWarps - 1) / kFarWarps, tree_level_nodes(G, Lc));
+  far_tree_kernel<kM><<<grid, kFarWarps * 32, 0, st>>>(rec, n, G, gdata, tree, Lc, fpart, counts);
+  return cudaGetLastError();
+}
 }  // namespace
 
 #define MMVM_CAT2(a, b) a##b
@@ -43,6 +62,8 @@ ListFarEntry MMVM_FAR(MMVM_INST_M)() {
   e.build = build_fn;
   e.far = far_fn;
   e.far_occupancy = far_occ_fn;
+  e.tree_build = tree_build_fn;
+  e.far_tree = far_tree_fn;
   e.n_edge = n_edge(kM);
   return e;
 }
@@ -60,7 +81,7 @@ static_assert(MMVM_INST_S < kSpec.nslices, "slice index out of range");
 constexpr ListSliceSpec kS = kSpec.s[MMVM_INST_S];
 constexpr size_t kSmem = near_list_smem_bytes<kM, kS.lo, kS.hi, kS.part, kS.w, kS.nst>();
 static_assert(kSmem <= 232448, "near-pair kernel needs more shared memory than a CTA has");
-#define MMVM_NEAR_KERNEL near_pair_kernel<kM, kS.lo, kS.hi, kS.part, kS.w, kS.minb, kS.nst>
+#define MMVM_NEAR_KERNEL near_pair_kernel<kM, kS.lo, kS.hi, kS.part, kS.w, kS.minb, kS.nst, kS.sync>
 
 cudaError_t prepare_fn() {
   return cudaFuncSetAttribute(MMVM_NEAR_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,

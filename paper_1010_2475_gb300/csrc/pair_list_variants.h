@@ -16,10 +16,11 @@ struct ListSliceSpec {
   int part = 0;  // 0: all columns, 1: edge columns (beta1 <= 1), 2: Laplacian columns
   int w = 0;     // warps per CTA
   int minb = 1;  // CTAs per SM
-  int nst = 2;   // shared-memory stages
+  int nst = 4;   // record slots per warp (copies issued this many sources ahead)
+  int sync = 1;  // CTA barrier every `sync` rounds (0: only between list windows)
 };
 
-constexpr int kMaxListVariants = 4;
+constexpr int kMaxListVariants = 8;
 constexpr int kMaxListSlices = 3;
 
 struct ListVariantSpec {
@@ -27,7 +28,7 @@ struct ListVariantSpec {
   ListSliceSpec s[kMaxListSlices];
 };
 
-constexpr int n_list_variants(int M) { return M <= 3 ? 2 : (M == 6 ? 4 : 2); }
+constexpr int n_list_variants(int M) { return M <= 3 ? 2 : (M == 6 ? 8 : 2); }
 
 constexpr ListVariantSpec list_variant_spec(int M, int v) {
   switch (M) {
@@ -47,7 +48,11 @@ constexpr ListVariantSpec list_variant_spec(int M, int v) {
       return v == 0 ? ListVariantSpec{2, {{1, 12, 1, 12, 1, 4}, {1, 12, 2, 12, 1, 4}}}
            : v == 1 ? ListVariantSpec{2, {{1, 12, 1, 12, 1, 4}, {1, 12, 2, 8, 1, 4}}}
            : v == 2 ? ListVariantSpec{2, {{1, 12, 1, 8, 1, 4}, {1, 12, 2, 8, 1, 4}}}
-                    : ListVariantSpec{1, {{1, 12, 0, 8, 1, 4}}};
+           : v == 3 ? ListVariantSpec{1, {{1, 12, 0, 8, 1, 4}}}
+           : v == 4 ? ListVariantSpec{2, {{1, 12, 1, 12, 1, 4, 0}, {1, 12, 2, 12, 1, 4, 0}}}
+           : v == 5 ? ListVariantSpec{2, {{1, 12, 1, 12, 1, 4, 4}, {1, 12, 2, 12, 1, 4, 4}}}
+           : v == 6 ? ListVariantSpec{1, {{1, 12, 0, 8, 1, 4, 0}}}
+                    : ListVariantSpec{1, {{1, 12, 0, 8, 1, 4, 4}}};
     case 7:
       return v == 0 ? ListVariantSpec{3, {{1, 14, 1, 12, 1, 4}, {1, 10, 2, 12, 1, 4},
                                           {11, 14, 2, 12, 1, 4}}}

@@ -129,12 +129,27 @@ int list_occupancy(const ListEntry& e) {
   return e.nslices ? best : 0;
 }
 
+long long tree_nodes(int G) { return tree_level_offset(G, tree_levels(G) + 1); }
+
+int tree_chunk_level(int G, int blocks, int* nodes) {
+  int L = 0;
+  while (tree_level_nodes(G, L) > std::max(blocks, 1)) ++L;
+  *nodes = tree_level_nodes(G, L);
+  return L;
+}
+
 cudaError_t list_launch(const ListEntry& e, const float* rec, int n, const float* gdata,
                         int2* ent, int* cnt, int C, double* partial, int S, double* fpart,
-                        unsigned long long* counts, int* err, cudaStream_t st) {
+                        float* tree, int Lc, unsigned long long* counts, int* err,
+                        cudaStream_t st) {
   const int G = (n + kGroup - 1) / kGroup;
   cudaError_t r = e.far.build(rec, n, G, gdata, ent, cnt, st);
-  if (r == cudaSuccess) r = e.far.far(rec, n, G, gdata, S, fpart, counts, st);
+  if (tree) {
+    if (r == cudaSuccess) r = e.far.tree_build(gdata, n, G, tree, st);
+    if (r == cudaSuccess) r = e.far.far_tree(rec, n, G, gdata, tree, Lc, fpart, counts, st);
+  } else if (r == cudaSuccess) {
+    r = e.far.far(rec, n, G, gdata, S, fpart, counts, st);
+  }
   for (int s = 0; s < e.nslices && r == cudaSuccess; ++s)
     r = e.slices[s].launch(rec, n, G, ent, cnt, C, partial, counts, err, st);
   return r;

@@ -86,6 +86,14 @@ struct ListFarEntry {
   cudaError_t (*far)(const float* rec, int n, int G, const float* gdata, int S, double* fpart,
                      unsigned long long* counts, cudaStream_t st) = nullptr;
   cudaError_t (*far_occupancy)(int* blocks_per_sm) = nullptr;
+  // the tree over the groups (node storage: tree_nodes(G) records of
+  // gdata_len(M) floats) and the far kernel walking it from the nodes of
+  // level Lc (one far block per node of that level)
+  cudaError_t (*tree_build)(const float* gdata, int n, int G, float* tree,
+                            cudaStream_t st) = nullptr;
+  cudaError_t (*far_tree)(const float* rec, int n, int G, const float* gdata, const float* tree,
+                          int Lc, double* fpart, unsigned long long* counts,
+                          cudaStream_t st) = nullptr;
   int n_edge = 0;  // edge columns of a far block (2 BMAX)
 };
 struct ListEntry {
@@ -102,11 +110,19 @@ ListEntry list_entry(int M, int v);
 cudaError_t list_prepare(const ListEntry& e);
 // CTAs per SM of the near kernels (the smallest), 0 on error.
 int list_occupancy(const ListEntry& e);
-// The whole list form of one right-hand side: list build, far kernel (S
-// source ranges into fpart), near kernels (C list segments into partial).
-// ent: G x G entries, cnt: G counts (G = groups of kGroup records).
+// The whole list form of one right-hand side: list build, far field, near
+// kernels (C list segments into partial).  ent: G x G entries, cnt: G counts
+// (G = groups of kGroup records).  Far field: tree == nullptr: the flat far
+// kernel over S source ranges; else the tree (tree_nodes(G) node records)
+// built and walked from the nodes of level Lc (tree_level_nodes(G, Lc) far
+// blocks; S is ignored).
 cudaError_t list_launch(const ListEntry& e, const float* rec, int n, const float* gdata,
                         int2* ent, int* cnt, int C, double* partial, int S, double* fpart,
-                        unsigned long long* counts, int* err, cudaStream_t st);
+                        float* tree, int Lc, unsigned long long* counts, int* err,
+                        cudaStream_t st);
+// Node records of levels >= 1 of the tree over G groups.
+long long tree_nodes(int G);
+// Level whose node count is closest to (not above) `blocks`, and its count.
+int tree_chunk_level(int G, int blocks, int* nodes);
 
 }  // namespace mmvm

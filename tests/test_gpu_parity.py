@@ -41,6 +41,13 @@ FP64_TOL = 1e-12
 MIXED_RHS_TOL = 5e-6
 
 
+def mixed_rhs_tol(order: int) -> float:
+    """Single right-hand side, mixed precision: 5e-6 up to order 6; above,
+    the FP32 rounding carried by the jet grows with its order n <= 3M
+    (~2 n u per entry, u = 2^-24), so the bound grows in proportion to M."""
+    return MIXED_RHS_TOL * max(1.0, order / 6.0)
+
+
 @pytest.fixture(scope="module")
 def mm():
     import paper_1010_2475_gb300 as mm
@@ -86,9 +93,9 @@ def test_multi_particle_rhs(mm, order, n, prec):
     else:
         ev, em = cond_errors(gx, gM, ox, oM, wl.x, wl.moments, t, order, wl.lam0, wl.nu,
                              np.arange(wl.n))
-        assert ev <= MIXED_RHS_TOL
+        assert ev <= mixed_rhs_tol(order)
         if order >= 2:
-            assert em <= MIXED_RHS_TOL
+            assert em <= mixed_rhs_tol(order)
 
 
 def test_literal_form_small(mm):
@@ -384,9 +391,58 @@ def test_tile_expansions_match_full_jet(mm, order, kind):
     ox, oM = oracle_rows_parallel(wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu, rows)
     ev, em = cond_errors(res["far"][0][rows], res["far"][1][rows], ox, oM, wl.x, wl.moments, 0.0,
                          order, wl.lam0, wl.nu, rows)
-    assert ev <= MIXED_RHS_TOL
+    assert ev <= mixed_rhs_tol(order)
     if order >= 2:
-        assert em <= MIXED_RHS_TOL
+        assert em <= mixed_rhs_tol(order)
+
+
+@pytest.mark.parametrize("order,kind", [(2, "disk"), (4, "disk"), (6, "patches"), (8, "disk")])
+def test_tree_far_field_matches_flat_and_full_jet(mm, order, kind, monkeypatch):
+    """The list form's far field through the tree over the groups (node
+    expansions built by exact shifts of the group expansions) against the
+    flat far kernel (one expansion per far group) and against every pair
+    through the full jet; the tree must evaluate fewer expansions for the
+    same pairs, and every ordered pair is covered once."""
+    if kind == "patches":
+        wl = mmvm_inputs.two_patches(n=8192, order=order, sigma=0.1, seed=600 + order)
+        rng = np.random.default_rng(order)
+        wl.moments[:, 3:] = rng.normal(size=wl.moments[:, 3:].shape) * 1e-3 \
+            * wl.moments[:, :1] * wl.lam0 ** 2
+    else:
+        wl = mmvm_inputs.random_disk(n=6000, order=order, radius=30.0, sigma=0.5,
+                                     seed=610 + order)
+    nv = mm.pair_variant_counts(order)[0]
+    res, work = {}, {}
+    for name, tree, flags in (("tree", "1", 0), ("flat", "0", 0),
+                              ("full", "0", mm.MMVM_FLAG_NO_FAR_FIELD)):
+        monkeypatch.setenv("MMVM_FAR_TREE", tree)
+        if flags == 0:
+            monkeypatch.setenv("MMVM_PAIR_VARIANT", str(nv))  # the first list variant
+        else:
+            monkeypatch.delenv("MMVM_PAIR_VARIANT", raising=False)
+        with mm.Context(order, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32, flags=flags) as ctx:
+            ctx.set_state(wl.x, wl.moments, 0.0)
+            cfg = mm.mmvm_pair_config(ctx.handle)
+            if flags == 0:
+                assert cfg["list_form"] == (2 if tree == "1" else 1)
+            res[name] = ctx.rhs()
+            work[name] = mm.mmvm_pair_work(ctx.handle)
+    for name in ("tree", "flat"):
+        near, far_pp, n_m2p, m2p_pairs = work[name]
+        assert near + far_pp + m2p_pairs == wl.n * wl.n
+    assert work["tree"][0] == work["flat"][0]  # the same near pairs
+    assert work["tree"][2] < work["flat"][2]   # fewer expansions evaluated
+    assert vel_error(res["tree"][0], res["full"][0]) <= 2e-6
+    assert vel_error(res["tree"][0], res["flat"][0]) <= 1e-6
+    if order >= 2:
+        assert rhs_error(res["tree"][1], res["full"][1], order, wl.lam0) <= 2e-6
+        assert rhs_error(res["tree"][1], res["flat"][1], order, wl.lam0) <= 1e-6
+    picks = switch_rows(wl.x, wl.moments, order, wl.lam0, per_kind=3)
+    rows = np.array(sorted({*np.random.default_rng(9).choice(wl.n, 8, replace=False),
+                            *(j for v in picks.values() for j in v)}))
+    ev, em = cond_errors(res["tree"][0][rows], res["tree"][1][rows], res["full"][0][rows],
+                         res["full"][1][rows], wl.x, wl.moments, 0.0, order, wl.lam0, wl.nu, rows)
+    assert ev <= 2e-6 and em <= 2e-6
 
 
 @pytest.mark.parametrize("order", [0, 1, 2, 3, 4, 5, 6, 7, 8])
@@ -414,7 +470,7 @@ def test_every_kernel_variant(mm, order, monkeypatch):
         ctx.close()
         assert cfg["variant"] == v
         seen.add(v)
-        assert vel_error_cond(gx, ox, sx) <= MIXED_RHS_TOL, cfg
+        assert vel_error_cond(gx, ox, sx) <= mixed_rhs_tol(order), cfg
         if order >= 1:
-            assert rhs_error_cond(gM, oM, sM, order, wl.lam0) <= MIXED_RHS_TOL, cfg
+            assert rhs_error_cond(gM, oM, sM, order, wl.lam0) <= mixed_rhs_tol(order), cfg
     assert len(seen) >= 2
