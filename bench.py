@@ -543,6 +543,64 @@ def separable_fmas(M: int) -> int:
     return tot
 
 
+def divergence_sweep(mm, M=60, eps=0.1, Re=1e3, dt=0.01, max_steps=400, chunk=5,
+                     deltas=(0.0, 1e-14, 1e-11, 1e-8, 1e-5)):
+    """Where does the order-60 FP64 trajectory leave the bounded range, and
+    how does that step move with the size of a perturbation of the initial
+    state?  Every moment of order >= 2 of the quadrupole state gets delta
+    times a fixed random draw in the weighted norm of the convergence
+    theorem (relative to the circulation); delta = 0 is the unperturbed FP64
+    run, whose only perturbation is rounding (~1e-16).  The divergence step
+    is the first checkpoint (every `chunk` steps) where the weighted norm of
+    the state exceeds 1e3 times its initial value or is not finite.  A step
+    that moves by a fixed amount per decade of delta says the blow-up is an
+    instability seeded at the perturbation's size: a wider floating-point
+    format (a smaller delta) moves it by that many steps per decade of
+    precision, no more."""
+    from tests.parity_util import weights
+
+    base = mmvm_inputs.single_quadrupole(order=M, eps=eps, sigma0=1.0, Re=Re, dt=dt)
+    w = weights(M, 1.0)
+    xi = np.random.default_rng(5).standard_normal(base.K)
+    xi[:3] = 0.0  # circulation and first moments unchanged
+    out = []
+    for d in deltas:
+        m0 = base.moments.copy()
+        m0[0] += d * xi / np.sqrt(w)
+        n0 = float(np.sqrt((m0[0] ** 2 * w).sum()))
+        step, growth = None, []
+        with mm.Context(M, base.lam0, base.nu, mm.MMVM_FP64) as c:
+            c.set_state(base.x, m0, 0.0)
+            done = 0
+            while done < max_steps:
+                c.step(dt, chunk)
+                done += chunk
+                _, m, _ = c.get_state()
+                nrm = float(np.sqrt((m[0] ** 2 * w).sum())) if np.isfinite(m).all() else np.inf
+                if d == 0.0:
+                    growth.append(round(math.log10(max(nrm / n0, 1e-300)), 3)
+                                  if np.isfinite(nrm) else None)
+                if not np.isfinite(nrm) or nrm > 1e3 * n0:
+                    step = done
+                    break
+        rec = {"delta": d, "divergence_step": step}
+        if d == 0.0:
+            rec["log10_norm_growth_every_%d_steps" % chunk] = growth
+        out.append(rec)
+    steps = [(r["delta"], r["divergence_step"]) for r in out if r["delta"] > 0
+             and r["divergence_step"] is not None]
+    slope = None
+    if len(steps) >= 2:
+        x = np.log10([d for d, _ in steps])
+        y = np.array([st for _, st in steps], dtype=float)
+        slope = float(np.polyfit(x, y, 1)[0])
+    return {"workload": f"order {M}, Lamb-Oseen core + quadrupole eps={eps}, Re={Re:g}, RK4 "
+                        f"dt={dt}, FP64 separable self term",
+            "runs": out, "steps_per_decade_of_delta": slope,
+            "criterion": "weighted norm above 1e3 x its initial value, or not finite, at a "
+                         f"checkpoint every {chunk} steps"}
+
+
 def run_single_high(args, mm):
     """Single particle at order 60 (see the module docstring)."""
     from oracle.rhs import lam_at, self_rhs_rows
@@ -608,6 +666,7 @@ def run_single_high(args, mm):
         "invariants": {"M00_unchanged": all(f[1][0, 0] == w.moments[0, 0]
                                             for f, (_, w) in zip(finals, ctxs))},
         "finite_steps": [steps if f is None else f for f in finite_until],
+        "divergence_vs_perturbation": divergence_sweep(mm),
         "note": "the FP64 trajectories at order 60 leave the finite range early (the last "
                 "finite 100-step mark is listed per instance: eps 1e-3, 1e-3, 1e-2, 1e-2, 0.1, "
                 "0.1 with Re 1e3, 1e4): once every moment is populated the per-row condition "

@@ -79,10 +79,53 @@ template <typename T> __device__ __forceinline__ T recip_of(int i);
 template <> __device__ __forceinline__ float recip_of<float>(int i) { return kRecip.f[i]; }
 template <> __device__ __forceinline__ double recip_of<double>(int i) { return kRecip.d[i]; }
 
+// Terms of the FP32 Kummer series at order P: the smallest KN with
+// prod_{j=1}^{KN} P / (P + 1 + j) below 2^-26, so that the terms dropped are
+// below FP32 rounding of the sum for every x <= P (the series is only used
+// there, or for x < 1).
+constexpr int kummer_terms(int P) {
+  double t = 1.0;
+  int k = 0;
+  while (t >= 1.0 / 67108864.0 && k < 120) {
+    ++k;
+    t *= (double)(P > 0 ? P : 1) / (double)(P + 1 + k);
+  }
+  return k + 1;
+}
+// Coefficients of the FP32 Horner form in y = x / Ps (Ps = max(P, 1)):
+// d_k = Ps^k / ((P+1)(P+2)...(P+k+1)), all in (0, 1/(P+1)] and far inside the
+// FP32 range (the unscaled 1 / ((P+1)...(P+k+1)) underflows it).
+template <int P>
+struct KummerCoef {
+  static constexpr int KN = kummer_terms(P);
+  static constexpr int PS = P > 0 ? P : 1;
+  float c[KN];
+  constexpr KummerCoef() : c() {
+    double v = 1.0;
+    for (int k = 0; k < KN; ++k) {
+      v = v * (k > 0 ? (double)PS : 1.0) / (double)(P + 1 + k);
+      c[k] = (float)v;
+    }
+  }
+};
+
 // sum_{k>=0} x^k / ((P+1)(P+2)...(P+k+1)) so that I_P(x) = e^{-x} * sum (x < P).
+// FP32: a fixed Horner form (every coefficient positive, so it is as
+// accurate as the term-by-term sum; no data-dependent trip count that would
+// split the lanes of a warp).
 template <int P, typename T>
 __device__ __forceinline__ T kummer_sum(T x) {
   constexpr bool f32 = std::is_same<T, float>::value;
+  if constexpr (f32) {
+    constexpr KummerCoef<P> kc{};
+    const T y = x * T(1.0 / KummerCoef<P>::PS);
+    T s = T(kc.c[KummerCoef<P>::KN - 1]);
+    static_for_down<0, KummerCoef<P>::KN - 1>([&](auto ic) {
+      constexpr int k = decltype(ic)::value;
+      s = fma(s, y, T(kc.c[k]));
+    });
+    return s;
+  }
   const T eps = f32 ? T(2e-8) : T(5e-18);
   constexpr int kmax = f32 ? 48 : 80;
   static_assert(P + kmax < 128, "reciprocal table too short");
@@ -158,13 +201,17 @@ struct PairNear {
     });
 
     if constexpr (PART != 2) {
-    // w[n-1] = zbar^n I_{n-1}(x), n = 1..NJ
-    T wr[NJ], wi[NJ];
-    if (x < T(40)) {
-      constexpr int P = NJ - 1;
-      T I[P + 1];
-      const T rxh = T(1) / x;  // inf at x == 0: those entries are replaced below
-      const T rx = rxh * (T(1) - xl * rxh);
+    // The holomorphic edge w_n = zbar^n I_{n-1}(x) is formed one order at a
+    // time inside the order loop (only the current order is live): for
+    // x < 40 from the table I_k and the running power zbar^n, for x >= 40 by
+    // the recursion w_{n+1} = (n zbar w_n - E zbar^{n+1}) / x, which neither
+    // under- nor overflows at large |b|.
+    constexpr int P = NJ - 1;
+    const bool small = x < T(40);
+    const T rxh = T(1) / x;  // inf at x == 0: those entries are replaced below
+    const T rx = rxh * (T(1) - xl * rxh);
+    T I[P + 1];
+    if (small) {
       I[0] = (T(1) - E) * rx;
       static_for<1, P + 1>([&](auto nc) {
         constexpr int k = decltype(nc)::value;
@@ -179,39 +226,12 @@ struct PairNear {
         });
         if (x < T(1)) I[0] = Id;
       }
-      T zr = b1 + l1, zi = -b2 - l2;
-      static_for<0, NJ>([&](auto nc) {
-        constexpr int k = decltype(nc)::value;
-        if constexpr (k > 0) {  // (zr + i zi) * ((b1 + l1) - i (b2 + l2)), two-term
-          const T tr = fma(zr, b1, fma(zi, b2, fma(zr, l1, zi * l2)));
-          const T ti = fma(zi, b1, fma(-zr, b2, fma(zi, l1, -zr * l2)));
-          zr = tr;
-          zi = ti;
-        }
-        wr[k] = zr * I[k];
-        wi[k] = zi * I[k];
-      });
-    } else {
-      const T rxh = T(1) / x;
-      const T rx = rxh * (T(1) - xl * rxh);
-      const T c1 = b1 + l1, c2 = b2 + l2;
-      T qr = E * c1, qi = -E * c2;  // E zbar^{n}
-      const T f0 = (T(1) - E) * rx;
-      wr[0] = c1 * f0;
-      wi[0] = -c2 * f0;
-      static_for<1, NJ>([&](auto nc) {
-        constexpr int k = decltype(nc)::value;  // order k+1 from order k
-        const T tr = qr * b1 + qi * b2;
-        const T ti = qi * b1 - qr * b2;
-        qr = tr;
-        qi = ti;
-        const T wr0 = wr[k - 1], wi0 = wi[k - 1];
-        const T pr = fma(wr0, b1, fma(wi0, b2, fma(wr0, l1, wi0 * l2)));
-        const T pi = fma(wi0, b1, fma(-wr0, b2, fma(wi0, l1, -wr0 * l2)));
-        wr[k] = (T(k) * pr - qr) * rx;
-        wi[k] = (T(k) * pi - qi) * rx;
-      });
     }
+    const T c1 = b1 + l1, c2 = b2 + l2;
+    T zr = c1, zi = -c2;            // zbar^n (x < 40)
+    T qr = E * c1, qi = -E * c2;    // E zbar^n (x >= 40)
+    T wr = c1 * ((T(1) - E) * rx);  // w_n (x >= 40)
+    T wi = -c2 * ((T(1) - E) * rx);
     // This pair's edge columns are summed apart from the running sums and
     // added to them once the last jet order feeding them is done (order k
     // takes jet orders k .. k + M): the terms of one pair cancel strongly,
@@ -220,11 +240,36 @@ struct PairNear {
     T pe[2 * (HI - LO + 1)];
 #pragma unroll
     for (int i = 0; i < 2 * (HI - LO + 1); ++i) pe[i] = T(0);
-    static_for<NLO, NJ + 1>([&](auto nc) {
+    static_for<1, NJ + 1>([&](auto nc) {
       constexpr int n = decltype(nc)::value;
+      T w_r, w_i;
+      if (small) {
+        if constexpr (n > 1) {  // (zr + i zi) * ((b1 + l1) - i (b2 + l2)), two-term
+          const T tr = fma(zr, b1, fma(zi, b2, fma(zr, l1, zi * l2)));
+          const T ti = fma(zi, b1, fma(-zr, b2, fma(zi, l1, -zr * l2)));
+          zr = tr;
+          zi = ti;
+        }
+        w_r = zr * I[n - 1];
+        w_i = zi * I[n - 1];
+      } else {
+        if constexpr (n > 1) {  // order n from order n - 1
+          const T tr = qr * b1 + qi * b2;
+          const T ti = qi * b1 - qr * b2;
+          qr = tr;
+          qi = ti;
+          const T pr = fma(wr, b1, fma(wi, b2, fma(wr, l1, wi * l2)));
+          const T pi = fma(wi, b1, fma(-wr, b2, fma(wi, l1, -wr * l2)));
+          wr = (T(n - 1) * pr - qr) * rx;
+          wi = (T(n - 1) * pi - qi) * rx;
+        }
+        w_r = wr;
+        w_i = wi;
+      }
+      if constexpr (n >= NLO) {
       const T f = T(((n - 1) & 1) ? -kInv4Pi : kInv4Pi) * wmask;
-      const T w_r = wr[n - 1] * f;
-      const T w_i = wi[n - 1] * f;
+      w_r *= f;
+      w_i *= f;
       T chi[n + 1];
       chi[0] = T(0);
       chi[1] = T(0);
@@ -276,6 +321,7 @@ struct PairNear {
         acc[bcol(0, kd) - B0] += pe[2 * (kd - LO)];
         acc[bcol(1, kd - 1) - B0] += pe[2 * (kd - LO) + 1];
       }
+      }  // n >= NLO
     });
     }  // PART != 2
     // Laplacian columns (beta1 >= 2): R[beta] = sum_m a_m e_(m + beta - 2 e1),

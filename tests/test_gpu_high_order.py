@@ -83,6 +83,29 @@ def test_order_60_dense_state(mm):
     _check_rows(gM, wl, t, rows)
 
 
+def test_order_60_dense_state_against_exact_rows(mm):
+    """The dense order-60 state at t = 0 (lambda = 1) against the exact
+    rational rows of tests/golden/order60_dense_exact.txt (oracle/exact.py):
+    every row within 64 eps of its absolute term sum S_k, and within 1e-6 of
+    the row itself where its condition number S_k / |dM_k| is below 1e8.
+    The second bound fails for a GPU row off by more than rounding on the
+    rows FP64 can resolve; the first is all FP64 promises on the rest (their
+    condition numbers reach 1e26)."""
+    import os
+
+    from tests.golden.make_order60_exact import dense_state, rows
+
+    g = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "order60_dense_exact.txt"))
+    wl = dense_state()
+    gx, gM = _gpu_rhs(mm, wl, 0.0)
+    v = gM[0, rows()]
+    d = np.abs(v - g[:, 2])
+    assert np.all(d <= 64 * EPS * g[:, 3]), (d / g[:, 3]).max()
+    good = g[:, 3] < 1e8 * np.abs(g[:, 2])
+    assert good.sum() >= 3
+    assert np.all(d[good] <= 1e-6 * np.abs(g[good, 2])), (d[good] / np.abs(g[good, 2])).max()
+
+
 def test_order_60_steps_keep_the_invariants(mm):
     """RK4 at order 60: the circulation M_00 never changes (its row has no
     term), the centre stays put, the first moments stay zero."""

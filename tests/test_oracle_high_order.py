@@ -86,3 +86,46 @@ def test_circulation_row_and_parity_rule():
     # the quadrupole does evolve: (2,0) - (0,2) turns into (1,1) (rotation)
     v2, a2 = self_rhs_rows(wl.moments[0], 1.0, order, [idx(1, 1), idx(3, 1)])
     assert np.all(a2 > 0) and abs(v2[0]) > 1e-3
+
+
+def test_exact_rows_match_fp64_rows_at_low_order():
+    """oracle/exact.py (rational arithmetic, one rounding at the end) against
+    the FP64 rows of self_rhs_rows on every row of a dense order-8 state at
+    lambda = 1: the two agree to the FP64 rounding of the row's terms."""
+    import mmvm_inputs
+    from oracle.exact import self_rows_exact, to_float
+    from oracle.rhs import self_rhs_rows
+
+    wl = mmvm_inputs.random_disk(n=1, order=8, radius=0.0, sigma=1.0, amp=0.05, seed=8)
+    rows = list(range(wl.K))
+    v, a = self_rows_exact(wl.moments[0], 8, rows)
+    ov, oa = self_rhs_rows(wl.moments[0], 1.0, 8, rows)
+    ev = np.array([to_float(x) for x in v])
+    ea = np.array([to_float(x) for x in a])
+    assert np.all(np.abs(ov - ev) <= 8 * 2.220446049250313e-16 * ea)
+    assert np.allclose(oa, ea, rtol=1e-13, atol=0.0)
+
+
+def test_order60_dense_rows_against_exact():
+    """The FP64 oracle at order 60 on a dense state (every one of the 1891
+    moments nonzero) against the exact rational rows of
+    tests/golden/order60_dense_exact.txt (written by make_order60_exact.py):
+    within 4 eps of each row's absolute term sum S_k, and within 1e-10 of
+    the row itself where the row's condition number S_k / |dM_k| is below
+    1e8 (the golden rows reach condition numbers of 1e26, where no FP64
+    evaluation can resolve the row at all)."""
+    import os
+
+    from tests.golden.make_order60_exact import dense_state, rows
+    from oracle.rhs import self_rhs_rows
+
+    g = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "order60_dense_exact.txt"))
+    wl = dense_state()
+    rr = rows()
+    v, a = self_rhs_rows(wl.moments[0], 1.0, 60, rr)
+    d = np.abs(v - g[:, 2])
+    assert np.all(d <= 4 * 2.220446049250313e-16 * g[:, 3])
+    good = g[:, 3] < 1e8 * np.abs(g[:, 2])
+    assert good.sum() >= 3
+    assert np.all(d[good] <= 1e-10 * np.abs(g[good, 2]))
+    assert np.allclose(a, g[:, 3], rtol=1e-12, atol=0.0)
