@@ -16,15 +16,30 @@ value      pair-interactions/s of the device-timed steps (state resident in HBM,
            timed region).
 e2e        the same metric through the C ABI with host buffers: set_state from
            pinned host memory, one step, get_state to pinned host memory.
-roofline   the all-pairs kernel (~97% of the step) against the FP32 FMA peak
-           measured in the same run (mmvm_alu_peak: a full-occupancy grid of
-           independent FMA chains; nominal 152 SMs x 128 lanes x 2 flop x
-           2.07 GHz = 80.5 TFLOP/s); the flops of one launch
-           are the work it did on each path (counted by the kernel: near
-           pairs, far pairs source by source, tile expansions) times that
-           path's flops (flops_per_pair, far_flops_per_pair, m2p_flops).
+roofline   the all-pairs kernels of one right-hand side (~95% of the step;
+           the autotuner's choice: the direct form, or the list form's list
+           build, tree, far-field and near-pair kernels) against the FP32 FMA
+           peak measured in the same run (mmvm_alu_peak: a full-occupancy
+           grid of independent FMA chains; nominal 152 SMs x 128 lanes x 2
+           flop x 2.07 GHz = 80.5 TFLOP/s); the flops of one launch are the
+           work it did on each path (counted by the kernels: near pairs, far
+           pairs source by source, expansions evaluated) times that path's
+           flops (flops_per_pair, far_flops_per_pair, m2p_flops).
+near_pairs_per_s, pairs_by_path_per_rhs  how the N^2 pairs of a right-hand
+           side were evaluated: through the full jet (near), the point-vortex
+           jet source by source, or inside expansions of far groups / tree
+           nodes (at FP32 rounding: the far field is the Gaussian-free tail).
 fp64       the plain FP64 form of the same right-hand side on the first 16384
-           particles of the workload (one right-hand side, device-timed).
+           particles of the workload (one right-hand side, device-timed),
+           beside mixed precision without and with the far field.
+mixed_vs_fp64_100_steps  the same comparison over 100 RK4 steps of the
+           recipe at N = 4096 (--prec-n): rates of the three forms, the gain
+           of the precision split and of the far field apart, and the
+           per-particle error of both mixed forms against FP64.
+single_m10 one particle at order 10 (66 moments), 500 FP64 RK4 steps: RHS/s,
+           coefficient terms/s and the error against the oracle's trajectory.
+random_disk_n4096  N = 4096, M = 4 random disk, up to 200 mixed RK4 steps:
+           throughput over the finite steps and the error against FP64.
 served     the served stream (independent random-disk solves: n log-uniform in
            [64, 8192], M in {2, 4, 8}, Re uniform in [100, 5000], 50-500 RK4
            steps of 0.01) through the continuous-batching server: a burst
@@ -41,7 +56,9 @@ single_m60 one particle at order 60 (1891 moments), Lamb-Oseen core plus a
            instances, 2000 RK4 steps of 0.01 each, FP64 separable self term
            (six contexts on their own streams); RHS evaluations/s, the
            multiply-adds of the separable passes against the measured FP64
-           peak, and sampled rows against the oracle at t = 0.
+           peak, sampled rows against the oracle at t = 0, and the step at
+           which the trajectory leaves the bounded range against the size of
+           a perturbation of the initial state.
 cpu_baseline the FP64 numpy oracle on sampled target rows against all sources,
            one host core; cpu_baseline_all_cores and --impl reference: one
            single-threaded oracle process per host core, each on its own rows.
@@ -825,7 +842,7 @@ def run_random_disk(args, mm, stream, device):
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
 KERNEL_SOURCES = ("common.cuh", "pair_kernel.cuh", "pair_launch.cuh", "pair_variants.h",
-                  "pair_inst.cu")
+                  "pair_inst.cu", "pair_list.cuh", "pair_list_variants.h", "pair_list_inst.cu")
 
 
 def kernel_source_hash() -> str:
@@ -1048,7 +1065,10 @@ def run_ours(args, wl, rank, world, local_rank):
                                              "launch (profiles/pair_kernel_traffic.json; null "
                                              "if the kernel sources or launch shape differ "
                                              "from the capture)",
-                             "kernel": "pair_kernel (all-pairs jet + contraction)",
+                             "kernel": ("list form: near_list_kernel, tree_level_kernel, "
+                                        "far_tree_kernel / far_pair_kernel, near_pair_kernel"
+                                        if pcfg.get("list_form") else
+                                        "pair_kernel (all-pairs jet + contraction)"),
                              "flops_per_pair": {"near": fpp, "far": ffp},
                              "flops_per_tile_expansion": fm2p,
                              "pairs_per_launch": {"near": near_l, "far_source_by_source": far_l,

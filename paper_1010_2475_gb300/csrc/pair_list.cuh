@@ -137,17 +137,6 @@ __global__ void near_list_kernel(const float* __restrict__ rec, int n, int G,
 }
 
 // ------------------------------------------------------------------ 2. near pairs
-// Column of the slice (numbered from B0) held in shared-memory slot q of a
-// column part (the inverse of PartCols::slot).
-template <int LO, int HI, int PART>
-__device__ __forceinline__ int slot_col(int q) {
-  using PC = PartCols<LO, HI, PART>;
-  int c = 0;
-  for (int k = 0; c < PC::NBL; ++c)
-    if (PC::in(c) && k++ == q) break;
-  return c;
-}
-
 template <int M, int LO, int HI, int PART, int W, int NST>
 struct NearListSmem {
   static constexpr int R = rec_len<float>(M);
@@ -330,16 +319,25 @@ __global__ void __launch_bounds__(W * 32, MINB)
     if (lane == 0 && wn) atomicAdd(counts, (unsigned long long)wn);
   }
   __syncthreads();  // every warp's (hi, lo) sums are in shared memory
-  // (hi, lo) sums of the W warps -> FP64, this part's columns of block y
+  // (hi, lo) sums of the W warps -> FP64, this part's columns of block y:
+  // column c (slot q) is summed by warp q mod W, one target per lane (the
+  // column of each slot is a compile-time constant)
   double* out = partial + (size_t)blockIdx.y * NB * n + (size_t)PN::B0 * n;
-  for (int idx = threadIdx.x; idx < NS * 32; idx += W * 32) {
-    const int q = idx >> 5, l = idx & 31, jj = tg * kGroup + l;
-    double v = 0.0;
+  const int jj = tg * kGroup + lane;
+  static_for<0, NBL>([&](auto cc) {
+    constexpr int c = decltype(cc)::value;
+    if constexpr (PC::in(c)) {
+      constexpr int q = PC::slot(c);
+      if (warp == q % W) {
+        double v = 0.0;
 #pragma unroll
-    for (int w = 0; w < W; ++w)
-      v += (double)acc_hi[(w * NS + q) * 32 + l] + (double)acc_lo[(w * NS + q) * 32 + l];
-    if (jj < n) out[(size_t)slot_col<LO, HI, PART>(q) * n + jj] = v;
-  }
+        for (int w = 0; w < W; ++w)
+          v += (double)acc_hi[(w * NS + q) * 32 + lane] +
+               (double)acc_lo[(w * NS + q) * 32 + lane];
+        if (jj < n) out[(size_t)c * n + jj] = v;
+      }
+    }
+  });
 }
 
 // ------------------------------------------------------------------ 3. far field

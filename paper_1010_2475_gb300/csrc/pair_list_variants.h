@@ -20,7 +20,7 @@ struct ListSliceSpec {
   int sync = 1;  // CTA barrier every `sync` rounds (0: only between list windows)
 };
 
-constexpr int kMaxListVariants = 8;
+constexpr int kMaxListVariants = 16;
 constexpr int kMaxListSlices = 3;
 
 struct ListVariantSpec {
