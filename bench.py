@@ -521,6 +521,66 @@ def run_served(args, mm):
     }
 
 
+def run_scaling(args, mm, stream, device):
+    """One right-hand side of the two-patch recipe at growing N, in the list
+    form with the tree far field: (a) the core shrinking as
+    sigma = 0.1 sqrt(65536 / N) (every particle keeps about the same number
+    of sources within the near-field radius, so the near work grows like N
+    and the far field decides the rest), (b) the benchmark's fixed
+    sigma = 0.1 (the near field is a fixed fraction of the N^2 pairs).
+    Device time of the all-pairs launches and of the whole right-hand side,
+    and the pairs by path."""
+    import torch
+
+    sizes = [int(v) for v in args.scaling.split(",") if v.strip()]
+    out = []
+    nv = mm.pair_variant_counts(6)[0]
+    saved = {k: os.environ.get(k) for k in ("MMVM_PAIR_VARIANT", "MMVM_FAR_TREE")}
+    os.environ["MMVM_PAIR_VARIANT"] = str(nv + 4)  # the list form's split, barrier-free variant
+    os.environ["MMVM_FAR_TREE"] = "1"
+    try:
+        for kind in ("sigma_scaled", "sigma_fixed"):
+            for n in sizes:
+                if kind == "sigma_fixed" and n > args.scaling_fixed_max:
+                    continue
+                sigma = 0.1 * math.sqrt(65536.0 / n) if kind == "sigma_scaled" else 0.1
+                wl = mmvm_inputs.two_patches(n=n, order=6, sigma=sigma, Re=2000.0, dt=0.05)
+                with mm.Context(6, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32, device=device) as c:
+                    mm.mmvm_set_stream(c.handle, stream.cuda_stream)
+                    c.set_state(wl.x, wl.moments, 0.0)
+                    mm.mmvm_enable_timing(c.handle, True)
+                    d_dx = torch.empty((n, 2), dtype=torch.float64, device=stream.device)
+                    d_dm = torch.empty((n, wl.K), dtype=torch.float64, device=stream.device)
+                    mm.mmvm_rhs_device(c.handle, d_dx.data_ptr(), d_dm.data_ptr())  # warm-up
+                    torch.cuda.synchronize(stream.device)
+                    mm.mmvm_pair_time(c.handle)
+                    w0 = mm.mmvm_pair_work(c.handle)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    mm.mmvm_rhs_device(c.handle, d_dx.data_ptr(), d_dm.data_ptr())
+                    e1.record(stream)
+                    e1.synchronize()
+                    rhs_ms = e0.elapsed_time(e1)
+                    pair_ms, _ = mm.mmvm_pair_time(c.handle)
+                    w1 = mm.mmvm_pair_work(c.handle)
+                    ok = bool(torch.isfinite(d_dm).all().item())
+                work = [int(b - a) for a, b in zip(w0, w1)]
+                out.append({"n": n, "sigma": sigma, "kind": kind, "rhs_ms": rhs_ms,
+                            "pair_ms": pair_ms, "value": n * n / (rhs_ms / 1e3), "unit": UNIT,
+                            "near_pairs": work[0], "far_pairs_source_by_source": work[1],
+                            "expansions": work[2], "pairs_in_expansions": work[3],
+                            "finite": ok})
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {"workload": "two co-rotating patches, M=6, one right-hand side per N (list form, "
+                        "tree far field)", "runs": out}
+
+
 def coefficient_terms(M: int) -> int:
     """(k, l, i, q) terms of the single-particle coefficient sums of
     eq:FinalSingleI/II per right-hand side at order M (every k, l with
@@ -1031,6 +1091,11 @@ def run_ours(args, wl, rank, world, local_rank):
     t_sec = time.perf_counter()
     disk = run_random_disk(args, mm, stream, local_rank) if args.disk_steps > 0 else None
     wall["random_disk"] = time.perf_counter() - t_sec
+    scaling = None
+    if args.scaling:
+        t_sec = time.perf_counter()
+        scaling = run_scaling(args, mm, stream, local_rank)
+        wall["scaling"] = time.perf_counter() - t_sec
 
     line = None
     pcfg = mm.mmvm_pair_config(ctx.handle)
@@ -1085,6 +1150,8 @@ def run_ours(args, wl, rank, world, local_rank):
                 "mixed_vs_fp64_100_steps": precision,
                 "single_m10": single_m10,
                 "random_disk_n4096": disk}
+        if scaling is not None:
+            line["scaling_n"] = scaling
         if args.serve_requests > 0:
             t_sec = time.perf_counter()
             line["served"] = run_served(args, mm)
@@ -1162,6 +1229,10 @@ def main():
                     help="FP64 RK4 steps of the order-10 single particle (0: skip)")
     ap.add_argument("--disk-steps", type=int, default=200,
                     help="RK4 steps of the N = 4096 random disk (0: skip)")
+    ap.add_argument("--scaling", type=str, default="",
+                    help="comma-separated N of the growing-N measurement (empty: skip)")
+    ap.add_argument("--scaling-fixed-max", type=int, default=262144,
+                    help="largest N of the fixed-sigma part of --scaling")
     ap.add_argument("--n", type=int, default=65536,
                     help="particles (the benchmark is 65536; smaller only for profiling)")
     args = ap.parse_args()

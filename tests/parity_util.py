@@ -164,20 +164,26 @@ def switch_rows(x, moments, order, lam, per_kind=8, seed=0):
     rng = np.random.default_rng(seed)
     perm, boxes, cen, rad = group_geometry(x, lam)
     xf = X_FAR[order]
-    dx = np.maximum(0.0, np.maximum(boxes[:, None, 0] - boxes[None, :, 1],
-                                    boxes[None, :, 0] - boxes[:, None, 1]))
-    dy = np.maximum(0.0, np.maximum(boxes[:, None, 2] - boxes[None, :, 3],
-                                    boxes[None, :, 2] - boxes[:, None, 3]))
-    d2 = dx * dx + dy * dy
-    band = ((d2 >= 0.9 * xf) & (d2 < 1.1 * xf)).sum(1)
-    # distance from each target box to each source centre
-    cx = np.maximum(0.0, np.maximum(boxes[:, None, 0] - cen[None, :, 0],
-                                    cen[None, :, 0] - boxes[:, None, 1]))
-    cy = np.maximum(0.0, np.maximum(boxes[:, None, 2] - cen[None, :, 1],
-                                    cen[None, :, 1] - boxes[:, None, 3]))
-    c2 = np.maximum(cx * cx + cy * cy, 1e-300)
-    ratio2 = rad[None, :] ** 2 / c2
-    m2p = ((d2 >= xf) & (ratio2 <= M2P_THETA2) & (ratio2 >= 0.81 * M2P_THETA2)).sum(1)
+    G = boxes.shape[0]
+    band = np.zeros(G, dtype=np.int64)
+    m2p = np.zeros(G, dtype=np.int64)
+    for t0 in range(0, G, 256):  # target groups in blocks (memory stays O(256 G))
+        tb = boxes[t0:t0 + 256]
+        dx = np.maximum(0.0, np.maximum(tb[:, None, 0] - boxes[None, :, 1],
+                                        boxes[None, :, 0] - tb[:, None, 1]))
+        dy = np.maximum(0.0, np.maximum(tb[:, None, 2] - boxes[None, :, 3],
+                                        boxes[None, :, 2] - tb[:, None, 3]))
+        d2 = dx * dx + dy * dy
+        band[t0:t0 + 256] = ((d2 >= 0.9 * xf) & (d2 < 1.1 * xf)).sum(1)
+        # distance from each target box to each source centre
+        cx = np.maximum(0.0, np.maximum(tb[:, None, 0] - cen[None, :, 0],
+                                        cen[None, :, 0] - tb[:, None, 1]))
+        cy = np.maximum(0.0, np.maximum(tb[:, None, 2] - cen[None, :, 1],
+                                        cen[None, :, 1] - tb[:, None, 3]))
+        c2 = np.maximum(cx * cx + cy * cy, 1e-300)
+        ratio2 = rad[None, :] ** 2 / c2
+        m2p[t0:t0 + 256] = ((d2 >= xf) & (ratio2 <= M2P_THETA2)
+                            & (ratio2 >= 0.81 * M2P_THETA2)).sum(1)
     size = (boxes[:, 1] - boxes[:, 0]) ** 2 + (boxes[:, 3] - boxes[:, 2]) ** 2
     n = x.shape[0]
 

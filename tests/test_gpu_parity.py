@@ -474,3 +474,40 @@ def test_every_kernel_variant(mm, order, monkeypatch):
         if order >= 1:
             assert rhs_error_cond(gM, oM, sM, order, wl.lam0) <= mixed_rhs_tol(order), cfg
     assert len(seen) >= 2
+
+
+@pytest.mark.parametrize("n", [262144])
+def test_tree_far_field_at_large_n(mm, n, monkeypatch):
+    """N = 262144 two patches with the core shrunk as sigma = 0.1 sqrt(65536 / N)
+    (the near work per particle of the benchmark): the list form with the
+    tree far field against every pair through the full jet on sampled rows
+    (2e-6 per particle, conditioning-aware) and against the oracle (the mixed
+    tolerance)."""
+    sigma = 0.1 * math.sqrt(65536.0 / n)
+    wl = mmvm_inputs.two_patches(n=n, order=6, sigma=sigma, seed=900)
+    nv = mm.pair_variant_counts(6)[0]
+    res = {}
+    for name, flags in (("tree", 0), ("full", mm.MMVM_FLAG_NO_FAR_FIELD)):
+        if flags == 0:
+            monkeypatch.setenv("MMVM_PAIR_VARIANT", str(nv + 4))
+            monkeypatch.setenv("MMVM_FAR_TREE", "1")
+        else:
+            monkeypatch.setenv("MMVM_PAIR_VARIANT", "0")
+        with mm.Context(6, wl.lam0, wl.nu, mm.MMVM_MIXED_FP32, flags=flags) as ctx:
+            ctx.set_state(wl.x, wl.moments, 0.0)
+            if flags == 0:
+                assert mm.mmvm_pair_config(ctx.handle)["list_form"] == 2
+            res[name] = ctx.rhs()
+            if flags == 0:
+                near, far_pp, n_m2p, m2p_pairs = mm.mmvm_pair_work(ctx.handle)
+    assert near + far_pp + m2p_pairs == wl.n * wl.n and n_m2p > 0 and far_pp > 0
+    picks = switch_rows(wl.x, wl.moments, 6, wl.lam0, per_kind=3)
+    rows = np.array(sorted({*np.random.default_rng(11).choice(wl.n, 9, replace=False),
+                            *(j for v in picks.values() for j in v)}))
+    ev, em = cond_errors(res["tree"][0][rows], res["tree"][1][rows], res["full"][0][rows],
+                         res["full"][1][rows], wl.x, wl.moments, 0.0, 6, wl.lam0, wl.nu, rows)
+    assert ev <= 2e-6 and em <= 2e-6
+    ox, oM = oracle_rows_parallel(wl.x, wl.moments, 0.0, 6, wl.lam0, wl.nu, rows)
+    ev, em = cond_errors(res["tree"][0][rows], res["tree"][1][rows], ox, oM, wl.x, wl.moments,
+                         0.0, 6, wl.lam0, wl.nu, rows)
+    assert ev <= MIXED_RHS_TOL and em <= MIXED_RHS_TOL
