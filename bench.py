@@ -105,6 +105,9 @@ def config_dict(wl, extra=None):
          "n": wl.n, "order": wl.order, "moments_per_particle": wl.K, "lambda0": wl.lam0,
          "Re": 1.0 / wl.nu, "dt": wl.dt,
          "precision": "mixed: FP32 pair jet/contraction, FP64 state/tables/finish/RK4",
+         "far_field": "on: pairs whose Gaussian tail is below FP32 rounding take the point-vortex "
+                      "jet, source by source or inside expansions of far groups / tree nodes "
+                      "(pairs_by_path_per_rhs; near_pairs_per_s counts the full-jet pairs)",
          "pairs_per_step": 4 * wl.n * wl.n,
          "l2": "flushed (256 MiB write) before every timed step, outside the timed region"}
     if extra:
@@ -132,6 +135,19 @@ def flops_per_pair(M: int) -> int:
     lap = 2 * ((bmax - 1) * K + (bmax - 1) * bmax // 2 * (M + 1)) if bmax >= 2 else 0
     jet = sum(4 * (n - 1) + 2 * min(n + 1, M + 2) + 8 for n in range(1, nj + 1))
     return edge + lap + jet + 16 * nj + 6 * (nj - 1) + 30
+
+
+def flops_per_pair_parts(M: int):
+    """flops_per_pair split by the list form's kernels: (edge part: the jet,
+    its edge contraction and the set-up; Laplacian part: the Hermite
+    functions and the separable sums); the two add up to flops_per_pair."""
+    K = (M + 1) * (M + 2) // 2
+    bmax = 2 * M if M > 0 else 1
+    nj = M + bmax
+    edge = 4 * bmax * K
+    lap = 2 * ((bmax - 1) * K + (bmax - 1) * bmax // 2 * (M + 1)) if bmax >= 2 else 0
+    jet = sum(4 * (n - 1) + 2 * min(n + 1, M + 2) + 8 for n in range(1, nj + 1))
+    return edge + jet + 16 * nj + 30, lap + 6 * (nj - 1)
 
 
 def far_flops_per_pair(M: int) -> int:
@@ -979,6 +995,7 @@ def run_ours(args, wl, rank, world, local_rank):
         ctx.step(wl.dt, 1)
     torch.cuda.synchronize(dev)
     mm.mmvm_pair_time(ctx.handle)
+    mm.mmvm_pair_time_parts(ctx.handle)  # drop the warm-up's split
     work0 = mm.mmvm_pair_work(ctx.handle)
     if dist:
         dist.barrier()
@@ -1001,6 +1018,7 @@ def run_ours(args, wl, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     launches = ctx.launches - launches0
     work1 = mm.mmvm_pair_work(ctx.handle)
+    parts_ms, parts_cnt = mm.mmvm_pair_time_parts(ctx.handle)
     total_ms = sum(step_ms)
     if dist:
         total_ms = max_over_ranks(total_ms, dist, dev)
@@ -1108,6 +1126,31 @@ def run_ours(args, wl, rank, world, local_rank):
                                              for a, b in zip(work0, work1)]
         flops_launch = near_l * fpp + far_l * ffp + m2p_l * fm2p
         achieved = flops_launch / avg_pair_s / 1e12
+        per_kernel = None
+        if parts_ms and parts_cnt:
+            # list form: [list build + tree, far field, near kernels...]
+            pcfg0 = mm.mmvm_pair_config(ctx.handle)
+            fe, fl = flops_per_pair_parts(wl.order)
+            names = ["near_list_kernel + tree_level_kernel",
+                     "far_tree_kernel" if pcfg0["list_form"] == 2 else "far_pair_kernel"]
+            flops = [0.0, far_l * ffp + m2p_l * fm2p]
+            near_parts = len(parts_ms) - 2
+            if near_parts == 1:
+                names.append("near_pair_kernel (all columns)")
+                flops.append(near_l * fpp)
+            else:
+                names.append("near_pair_kernel edge part")
+                flops.append(near_l * fe)
+                for k in range(near_parts - 1):
+                    names.append(f"near_pair_kernel Laplacian part {k + 1}")
+                    flops.append(near_l * fl / (near_parts - 1))
+            per_kernel = []
+            for nm, f, t in zip(names, flops, parts_ms):
+                ms_rhs = t / parts_cnt
+                tf = f / (ms_rhs / 1e3) / 1e12 if ms_rhs > 0 and f > 0 else None
+                per_kernel.append({"kernel": nm, "ms_per_rhs": ms_rhs, "flops_per_rhs": f,
+                                   "achieved_tflops": tf,
+                                   "frac": tf / fp32_peak if tf is not None else None})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -1145,7 +1188,11 @@ def run_ours(args, wl, rank, world, local_rank):
                              "peak_note": "of measured: FP32 FMA peak measured in this run "
                                           "(mmvm_alu_peak); nominal 152 SMs x 128 lanes x 2 "
                                           "flop x 2.07 GHz = %.1f TFLOP/s" % FP32_PEAK_TFLOPS,
-                             "frac_of_nominal": achieved / FP32_PEAK_TFLOPS},
+                             "frac_of_nominal": achieved / FP32_PEAK_TFLOPS,
+                             "per_kernel": per_kernel,
+                             "per_kernel_note": "event-timed between the list form's launches; "
+                                                "the Laplacian flops of a split near part are "
+                                                "shared evenly between its kernels"},
                 "fp64": fp64,
                 "mixed_vs_fp64_100_steps": precision,
                 "single_m10": single_m10,

@@ -160,6 +160,15 @@ int64_t mmvm_launch_count(const mmvm_ctx* ctx);
 int mmvm_enable_timing(mmvm_ctx* ctx, int on);
 int mmvm_pair_time(mmvm_ctx* ctx, double* ms, int64_t* count);
 
+/* The same time split by kernel for the list form (the all-pairs variants
+ * with mmvm_pair_config out[6] > 0): ms[0] the list build and the tree,
+ * ms[1] the far-field kernel, ms[2 ..] each near kernel; summed over the
+ * right-hand sides that mmvm_pair_time has read since the previous call of
+ * this function (*count of them), *nparts = 2 + near kernels (0 for the
+ * direct form).  ms must hold max_parts values.                             */
+int mmvm_pair_time_parts(mmvm_ctx* ctx, double* ms, int32_t max_parts, int32_t* nparts,
+                         int64_t* count);
+
 /* All-pairs kernel configuration in use for the loaded state, out[0..7]:
  *  [0] variant index: 0 .. nv-1 the direct form (source tiles shared by the
  *      target groups of a CTA), nv .. nv+nl-1 the interaction-list form

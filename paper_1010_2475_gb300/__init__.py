@@ -54,7 +54,8 @@ EXPORTS = (
     "mmvm_step", "mmvm_set_stream", "mmvm_synchronize", "mmvm_num_particles",
     "mmvm_num_moments", "mmvm_launch_count", "mmvm_last_error", "mmvm_last_error_string",
     "mmvm_enable_timing",
-    "mmvm_pair_time", "mmvm_pair_config", "mmvm_pair_variant_counts", "mmvm_pair_counts",
+    "mmvm_pair_time", "mmvm_pair_time_parts", "mmvm_pair_config", "mmvm_pair_variant_counts",
+    "mmvm_pair_counts",
     "mmvm_pair_work", "mmvm_alu_peak",
     "mmvm_rhs_noalloc", "mmvm_integrate", "mmvm_vorticity", "mmvm_nonaxi_enstrophy", "mmvm_server_create", "mmvm_server_destroy", "mmvm_submit",
     "mmvm_poll", "mmvm_server_stats", "mmvm_request_footprint",
@@ -149,6 +150,9 @@ def load_library(path: str = LIB_PATH):
     lib.mmvm_enable_timing.restype = ctypes.c_int
     lib.mmvm_pair_time.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
     lib.mmvm_pair_time.restype = ctypes.c_int
+    lib.mmvm_pair_time_parts.argtypes = [P, D, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int64)]
+    lib.mmvm_pair_time_parts.restype = ctypes.c_int
     lib.mmvm_integrate.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_int64,
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -289,6 +293,16 @@ def mmvm_pair_time(h):
     cnt = ctypes.c_int64()
     _check(load_library().mmvm_pair_time(h, ctypes.byref(ms), ctypes.byref(cnt)))
     return ms.value, cnt.value
+
+
+def mmvm_pair_time_parts(h):
+    """(per-kernel ms list of the list form: [list build + tree, far field,
+    near kernels...], right-hand sides summed) since the previous call."""
+    ms = (ctypes.c_double * 8)()
+    npart = ctypes.c_int32()
+    cnt = ctypes.c_int64()
+    _check(load_library().mmvm_pair_time_parts(h, ms, 8, ctypes.byref(npart), ctypes.byref(cnt)))
+    return list(ms)[:npart.value], cnt.value
 
 
 def mmvm_integrate(h, t_end: float, h0: float = 0.01, rtol: float = 1e-8, atol: float = 1e-8,

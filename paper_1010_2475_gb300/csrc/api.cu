@@ -123,6 +123,14 @@ struct mmvm_ctx {
   bool timing = false;
   cudaEvent_t ev[5][2] = {};
   bool ev_pending[5] = {};
+  // list form: marks between its kernels (after list build + tree, after the
+  // far kernel, after each near kernel) and their summed times since the last
+  // mmvm_pair_time_parts call
+  static constexpr int kMarks = 2 + mmvm::kMaxListSlices;
+  cudaEvent_t evm[5][kMarks] = {};
+  bool evm_pending[5] = {};
+  double parts_ms[kMarks] = {};
+  int64_t parts_count = 0;
 
   double* t_dev() { return scal.p; }
   double* dt_dev() { return scal.p + 1; }
@@ -300,7 +308,8 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
       MMVM_CK(mmvm::list_launch(c->le, reinterpret_cast<const float*>(c->rec.p), n, c->gbox.p,
                                 c->lent.p, c->lcnt.p, c->lseg, c->partial.p, c->lfar, c->fpart.p,
                                 c->tree ? c->tnodes.p : nullptr, c->lc, c->counts.p, c->errf.p,
-                                c->st));
+                                c->st, c->timing ? c->evm[slot] : nullptr));
+      if (c->timing) c->evm_pending[slot] = true;
     } else {
       MMVM_CK(mmvm::pair_launch(c->pe, c->rec.p, n, c->chunks, c->S,
                                 c->far ? c->gbox.p : nullptr, c->partial.p, 0, c->st,
@@ -771,6 +780,9 @@ void mmvm_destroy(mmvm_ctx* c) {
   for (auto& pr : c->ev)
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
+  for (auto& pr : c->evm)
+    for (auto& e : pr)
+      if (e) cudaEventDestroy(e);
   for (auto* b : {&c->x, &c->m, &c->xs, &c->ms, &c->xsum, &c->msum, &c->rdx, &c->rdm, &c->scal,
                   &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr, &c->dpts, &c->dval, &c->dring, &c->dk,
                   &c->fpart})
@@ -1186,10 +1198,13 @@ int mmvm_enable_timing(mmvm_ctx* c, int on) {
   if (on && !c->ev[0][0]) {
     for (auto& pr : c->ev)
       for (auto& e : pr) MMVM_CK(cudaEventCreate(&e));
+    for (auto& pr : c->evm)
+      for (auto& e : pr) MMVM_CK(cudaEventCreate(&e));
   }
   if (c->timing != (on != 0)) c->drop_graph();  // re-capture with or without events
   c->timing = on != 0;
   for (bool& p : c->ev_pending) p = false;
+  for (bool& p : c->evm_pending) p = false;
   return MMVM_OK;
 }
 
@@ -1207,7 +1222,30 @@ int mmvm_pair_time(mmvm_ctx* c, double* ms, int64_t* count) {
     *ms += e;
     *count += 1;
     c->ev_pending[s] = false;
+    if (c->evm_pending[s] && c->list) {
+      cudaEvent_t prev = c->ev[s][0];
+      for (int k = 0; k < 2 + c->le.nslices; ++k) {
+        float p = 0.f;
+        MMVM_CK(cudaEventElapsedTime(&p, prev, c->evm[s][k]));
+        c->parts_ms[k] += p;
+        prev = c->evm[s][k];
+      }
+      c->parts_count += 1;
+    }
+    c->evm_pending[s] = false;
   }
+  return MMVM_OK;
+}
+
+int mmvm_pair_time_parts(mmvm_ctx* c, double* ms, int32_t max_parts, int32_t* nparts,
+                         int64_t* count) {
+  if (!c || !ms || !nparts || !count) return fail(MMVM_E_INVALID_ARG, "null argument");
+  const int np = c->list ? 2 + c->le.nslices : 0;
+  *nparts = np;
+  *count = c->parts_count;
+  for (int k = 0; k < std::min<int>(np, max_parts); ++k) ms[k] = c->parts_ms[k];
+  for (double& v : c->parts_ms) v = 0.0;
+  c->parts_count = 0;
   return MMVM_OK;
 }
 

@@ -141,17 +141,19 @@ int tree_chunk_level(int G, int blocks, int* nodes) {
 cudaError_t list_launch(const ListEntry& e, const float* rec, int n, const float* gdata,
                         int2* ent, int* cnt, int C, double* partial, int S, double* fpart,
                         float* tree, int Lc, unsigned long long* counts, int* err,
-                        cudaStream_t st) {
+                        cudaStream_t st, cudaEvent_t* marks) {
   const int G = (n + kGroup - 1) / kGroup;
   cudaError_t r = e.far.build(rec, n, G, gdata, ent, cnt, st);
-  if (tree) {
-    if (r == cudaSuccess) r = e.far.tree_build(gdata, n, G, tree, st);
-    if (r == cudaSuccess) r = e.far.far_tree(rec, n, G, gdata, tree, Lc, fpart, counts, st);
-  } else if (r == cudaSuccess) {
-    r = e.far.far(rec, n, G, gdata, S, fpart, counts, st);
-  }
-  for (int s = 0; s < e.nslices && r == cudaSuccess; ++s)
+  if (tree && r == cudaSuccess) r = e.far.tree_build(gdata, n, G, tree, st);
+  if (marks && r == cudaSuccess) r = cudaEventRecord(marks[0], st);
+  if (r == cudaSuccess)
+    r = tree ? e.far.far_tree(rec, n, G, gdata, tree, Lc, fpart, counts, st)
+             : e.far.far(rec, n, G, gdata, S, fpart, counts, st);
+  if (marks && r == cudaSuccess) r = cudaEventRecord(marks[1], st);
+  for (int s = 0; s < e.nslices && r == cudaSuccess; ++s) {
     r = e.slices[s].launch(rec, n, G, ent, cnt, C, partial, counts, err, st);
+    if (marks && r == cudaSuccess) r = cudaEventRecord(marks[2 + s], st);
+  }
   return r;
 }
 

@@ -116,10 +116,12 @@ int list_occupancy(const ListEntry& e);
 // kernel over S source ranges; else the tree (tree_nodes(G) node records)
 // built and walked from the nodes of level Lc (tree_level_nodes(G, Lc) far
 // blocks; S is ignored).
+// marks (nullable, 2 + nslices events): recorded after the list build and
+// tree, after the far kernel and after each near kernel (per-kernel timing).
 cudaError_t list_launch(const ListEntry& e, const float* rec, int n, const float* gdata,
                         int2* ent, int* cnt, int C, double* partial, int S, double* fpart,
                         float* tree, int Lc, unsigned long long* counts, int* err,
-                        cudaStream_t st);
+                        cudaStream_t st, cudaEvent_t* marks = nullptr);
 // Node records of levels >= 1 of the tree over G groups.
 long long tree_nodes(int G);
 // Level whose node count is closest to (not above) `blocks`, and its count.

@@ -10,3 +10,12 @@ def test_coefficient_terms_count_the_literal_sums():
                 for (k1, k2) in mi for (l1, l2) in mi)
         assert coefficient_terms(M) == n
     assert coefficient_terms(60) == 945439488
+
+
+def test_flops_split_adds_up():
+    """The list form's per-kernel split of the near-pair flop count adds up
+    to the count of a whole near pair at every order."""
+    import bench
+
+    for M in range(0, 9):
+        assert sum(bench.flops_per_pair_parts(M)) == bench.flops_per_pair(M)
