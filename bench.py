@@ -58,7 +58,8 @@ single_m60 one particle at order 60 (1891 moments), Lamb-Oseen core plus a
            multiply-adds of the separable passes against the measured FP64
            peak, sampled rows against the oracle at t = 0, and the step at
            which the trajectory leaves the bounded range against the size of
-           a perturbation of the initial state.
+           a perturbation of the initial state and against the time step
+           (order 48 as the control).
 cpu_baseline the FP64 numpy oracle on sampled target rows against all sources,
            one host core; cpu_baseline_all_cores and --impl reference: one
            single-threaded oracle process per host core, each on its own rows.
@@ -694,6 +695,49 @@ def divergence_sweep(mm, M=60, eps=0.1, Re=1e3, dt=0.01, max_steps=400, chunk=5,
                          f"checkpoint every {chunk} steps"}
 
 
+def divergence_vs_dt(mm, M=60, Re=1e3, t_end=5.0, eps_list=(0.1, 1e-2),
+                     dts=(0.01, 0.005, 0.0025, 0.00125), check_t=0.05):
+    """Does the order-60 FP64 trajectory leave the bounded range because of
+    RK4's stability limit (a stiff mode that a smaller step would resolve)
+    or because the truncated system itself has a growing mode?  The same
+    state is run with the step halved three times; the divergence time (the
+    first check, every check_t time units, where the weighted norm exceeds
+    1e3 times its initial value or is not finite) is listed per step.  A
+    time that does not move with the step rules out the integrator.  Order 48
+    from the same states is the control."""
+    from tests.parity_util import weights
+
+    out = []
+    for order in (M, 48):
+        w = weights(order, 1.0)
+        for eps in eps_list:
+            rec = {"order": order, "eps": eps, "divergence_time": {}}
+            for dt in dts:
+                base = mmvm_inputs.single_quadrupole(order=order, eps=eps, sigma0=1.0, Re=Re,
+                                                     dt=dt)
+                n0 = float(np.sqrt((base.moments[0] ** 2 * w).sum()))
+                chunk = max(1, int(round(check_t / dt)))
+                t_div, done = None, 0
+                with mm.Context(order, base.lam0, base.nu, mm.MMVM_FP64) as c:
+                    c.set_state(base.x, base.moments, 0.0)
+                    while done * dt < t_end - 1e-9:
+                        c.step(dt, chunk)
+                        done += chunk
+                        _, m, _ = c.get_state()
+                        nrm = float(np.sqrt((m[0] ** 2 * w).sum())) \
+                            if np.isfinite(m).all() else np.inf
+                        if not np.isfinite(nrm) or nrm > 1e3 * n0:
+                            t_div = round(done * dt, 6)
+                            break
+                rec["divergence_time"][str(dt)] = t_div
+            out.append(rec)
+    return {"workload": f"Lamb-Oseen core + quadrupole, Re={Re:g}, FP64 separable self term, "
+                        f"RK4 to t={t_end} with dt in {list(dts)}",
+            "runs": out,
+            "criterion": "weighted norm above 1e3 x its initial value, or not finite, at a "
+                         f"check every {check_t} time units; null: bounded to t_end"}
+
+
 def run_single_high(args, mm):
     """Single particle at order 60 (see the module docstring)."""
     from oracle.rhs import lam_at, self_rhs_rows
@@ -760,6 +804,7 @@ def run_single_high(args, mm):
                                             for f, (_, w) in zip(finals, ctxs))},
         "finite_steps": [steps if f is None else f for f in finite_until],
         "divergence_vs_perturbation": divergence_sweep(mm),
+        "divergence_vs_dt": divergence_vs_dt(mm),
         "note": "the FP64 trajectories at order 60 leave the finite range early (the last "
                 "finite 100-step mark is listed per instance: eps 1e-3, 1e-3, 1e-2, 1e-2, 0.1, "
                 "0.1 with Re 1e3, 1e4): once every moment is populated the per-row condition "

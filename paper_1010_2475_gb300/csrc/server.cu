@@ -585,7 +585,10 @@ cudaError_t complete_tick(mmvm_server* s, Batch& b) {
                                  cudaMemcpyDeviceToHost, b.st)) != cudaSuccess)
     return e;
   if ((e = cudaStreamSynchronize(b.st)) != cudaSuccess) return e;
+  // the members that are done or diverged: their state copies are queued
+  // together and waited for once
   std::vector<Request*> keep;
+  std::vector<size_t> done;
   for (size_t i = 0; i < nm; ++i) {
     Request* r = b.members[i];
     r->steps_done += 1;
@@ -594,13 +597,17 @@ cudaError_t complete_tick(mmvm_server* s, Batch& b) {
       keep.push_back(r);
       continue;
     }
+    done.push_back(i);
     e = cudaMemcpyAsync(r->x.data(), r->d_state, r->x.size() * sizeof(double),
                         cudaMemcpyDeviceToHost, b.st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(r->m.data(), r->d_state + 2 * r->n, r->m.size() * sizeof(double),
                           cudaMemcpyDeviceToHost, b.st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b.st);
     if (e != cudaSuccess) return e;
+  }
+  if (!done.empty() && (e = cudaStreamSynchronize(b.st)) != cudaSuccess) return e;
+  for (size_t i : done) {
+    Request* r = b.members[i];
     cudaFreeAsync(r->d_state, b.st);
     r->d_state = nullptr;
     int status = MMVM_OK;
