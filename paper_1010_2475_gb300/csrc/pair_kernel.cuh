@@ -40,8 +40,9 @@
 //    c_0 + i c_1 = 2 i^n [ d^n psi/dz^n - 2^{-n} sum_a C(n,a) (-i)^{n-a} chi_a ].
 // I_k is formed by the upward recurrence I_k = (k I_{k-1} - e^{-x})/x where it
 // is stable (k <= x) and downward from a Kummer series at the top order
-// otherwise; for x >= 40 the edge zbar^n I_{n-1} itself is run upward in
-// complex arithmetic so that nothing under- or overflows at large |b|.
+// otherwise; for x >= table_x(P) (well beyond the near field, and the self
+// pair, which is moved far away) the edge zbar^n I_{n-1} itself is run upward
+// in complex arithmetic so that nothing under- or overflows at large |b|.
 //
 // FP32 mode carries the separation as an exact pair b = b_hi + b_lo (the
 // records hold zeta as (hi, lo) floats).  The Gaussian factors are sensitive
@@ -140,6 +141,13 @@ __device__ __forceinline__ T kummer_sum(T x) {
   return s;
 }
 
+// Largest x = |b|^2 at which the edge takes the table form zbar^n I_{n-1}(x)
+// up to n = P + 1 in FP32: there I_P(x) ~ P! / x^(P+1) stays above 1e-35 and
+// |zbar|^(P+1) below 1e30, inside the normal FP32 range (I_17(300) ~ 1e-30,
+// I_23(200) ~ 1e-33).  In FP32 the two forms agree to ~2e-6 of |w_n| at
+// n = 18 over 20 <= x <= 400.
+__host__ __device__ constexpr float table_x(int P) { return P <= 17 ? 300.f : 200.f; }
+
 // Outputs of one order slice: Psi[beta] with LO <= |beta| <= HI, i.e. the
 // columns [B0, B1).  They need the jet orders LO .. HI + M only.  PART 1
 // accumulates only the edge columns (the jet), PART 2 only the Laplacian
@@ -203,11 +211,13 @@ struct PairNear {
     if constexpr (PART != 2) {
     // The holomorphic edge w_n = zbar^n I_{n-1}(x) is formed one order at a
     // time inside the order loop (only the current order is live): for
-    // x < 40 from the table I_k and the running power zbar^n, for x >= 40 by
-    // the recursion w_{n+1} = (n zbar w_n - E zbar^{n+1}) / x, which neither
-    // under- nor overflows at large |b|.
+    // x < table_x(P) from the table I_k and the running power zbar^n, beyond
+    // by the recursion w_{n+1} = (n zbar w_n - E zbar^{n+1}) / x, which
+    // neither under- nor overflows at large |b|.  Near pairs lie below the
+    // threshold, so the lanes of a warp agree and the per-order test does
+    // not split the warp.
     constexpr int P = NJ - 1;
-    const bool small = x < T(40);
+    const bool small = x < T(table_x(P));
     const T rxh = T(1) / x;  // inf at x == 0: those entries are replaced below
     const T rx = rxh * (T(1) - xl * rxh);
     T I[P + 1];
@@ -228,9 +238,9 @@ struct PairNear {
       }
     }
     const T c1 = b1 + l1, c2 = b2 + l2;
-    T zr = c1, zi = -c2;            // zbar^n (x < 40)
-    T qr = E * c1, qi = -E * c2;    // E zbar^n (x >= 40)
-    T wr = c1 * ((T(1) - E) * rx);  // w_n (x >= 40)
+    T zr = c1, zi = -c2;            // zbar^n (table form)
+    T qr = E * c1, qi = -E * c2;    // E zbar^n (recursion)
+    T wr = c1 * ((T(1) - E) * rx);  // w_n (recursion)
     T wi = -c2 * ((T(1) - E) * rx);
     // This pair's edge columns are summed apart from the running sums and
     // added to them once the last jet order feeding them is done (order k
