@@ -141,14 +141,23 @@ template <int M, int LO, int HI, int PART, int W, int NST>
 struct NearListSmem {
   static constexpr int R = rec_len<float>(M);
   static constexpr int NS = PartCols<LO, HI, PART>::NS;
-  static constexpr int WIN = 256;  // list entries per window
   // per warp: NST slots of one source record each, NST mbarriers
   static constexpr size_t slot_off = 0;
   static constexpr size_t acc_off = slot_off + (size_t)W * NST * R * 4;
   static constexpr size_t ent_off = acc_off + (size_t)2 * W * NS * 32 * 4;
+  // list entries per window: 256, or 128 where the (hi, lo) sums leave too
+  // little shared memory for the window's source list
+  static constexpr size_t win_bytes(int win) {
+    return ((ent_off + (size_t)win * 8 + (win + 1) * 4 + (size_t)win * 64 + 7) / 8 * 8) +
+           (size_t)W * NST * 8;
+  }
+  static constexpr int WIN = win_bytes(256) <= 232448 ? 256 : 128;
   static constexpr size_t pref_off = ent_off + (size_t)WIN * 8;
-  static constexpr size_t bar_off = (pref_off + (WIN + 1) * 4 + 7) / 8 * 8;
+  // the window's near sources in order, (entry << 5) | lane of the source
+  static constexpr size_t src_off = pref_off + (WIN + 1) * 4;
+  static constexpr size_t bar_off = (src_off + (size_t)WIN * 32 * 2 + 7) / 8 * 8;
   static constexpr size_t bytes = bar_off + (size_t)W * NST * 8;
+  static_assert(WIN * 32 <= 65536, "source entries are 16-bit");
   static_assert((R * 4) % 16 == 0, "a record must be a whole number of 16-byte chunks");
 };
 
@@ -161,8 +170,9 @@ constexpr int kNearFlush = 32;
 // this part's columns of partial block blockIdx.y ([NB][n] FP64).
 //
 // The segment is taken in windows of WIN list entries: warp 0 forms the
-// exclusive prefix sums of the entries' near counts, then round k gives warp
-// w the (k W + w)-th near source of the window.  Each warp brings its own
+// exclusive prefix sums of the entries' near counts, the CTA lists the
+// window's near sources in order (16-bit entry and lane), then round k gives
+// warp w the (k W + w)-th near source of the window.  Each warp brings its own
 // sources into NST record slots of its own, one bulk copy per source issued
 // by its lane 0 NST rounds ahead (completion on the slot's mbarrier), so a
 // warp only ever waits for copies it issued itself.  SYNC > 0: a CTA barrier
@@ -186,6 +196,7 @@ __global__ void __launch_bounds__(W * 32, MINB)
   float* acc_lo = acc_hi + W * NS * 32;
   int2* ent_s = reinterpret_cast<int2*>(smem_list + L::ent_off);
   int* pref_s = reinterpret_cast<int*>(smem_list + L::pref_off);
+  unsigned short* src_s = reinterpret_cast<unsigned short*>(smem_list + L::src_off);
   unsigned long long* bar =
       reinterpret_cast<unsigned long long*>(smem_list + L::bar_off) + (size_t)warp * NST;
 
@@ -258,15 +269,23 @@ __global__ void __launch_bounds__(W * 32, MINB)
       if (lane == 31) pref_s[WIN] = incl;
     }
     __syncthreads();
+    // every thread lists the near sources of one entry at the entry's offset
+    for (int e = threadIdx.x; e < nw; e += W * 32) {
+      unsigned m = (unsigned)ent_s[e].y;
+      int q = pref_s[e];
+      while (m) {
+        src_s[q++] = (unsigned short)((e << 5) | (__ffs(m) - 1));
+        m &= m - 1;
+      }
+    }
+    __syncthreads();
     const int Lw = pref_s[WIN];
     const int mine = Lw > warp ? (Lw - 1 - warp) / W + 1 : 0;  // this warp's sources
     // lane 0: bulk copy of the k-th source of this warp into slot (tbase + k) % NST
-    int ei = 0;  // lane 0's entry pointer for the copies (positions only grow)
     auto issue = [&](int k) {
-      const int p = warp + k * W;
-      while (pref_s[ei + 1] <= p) ++ei;
-      const int2 en = ent_s[ei];
-      const int ls = __fns((unsigned)en.y, 0, p - pref_s[ei] + 1);
+      const unsigned sv = src_s[warp + k * W];
+      const int ls = (int)(sv & 31u);
+      const int2 en = ent_s[sv >> 5];
       const int t = tbase + k;
       unsigned long long* b = bar + t % NST;
       mbar_arrive_expect_tx(b, (unsigned)(R * 4));
@@ -275,13 +294,12 @@ __global__ void __launch_bounds__(W * 32, MINB)
     };
     if (lane == 0)
       for (int k = 0; k < min(NST, mine); ++k) issue(k);
-    int ep = 0;  // this warp's entry pointer for the sources it evaluates
     for (int k = 0; k * W < Lw; ++k) {
       const int p = warp + k * W;
       if (p < Lw) {
-        while (pref_s[ep + 1] <= p) ++ep;
-        const int2 en = ent_s[ep];
-        const int ls = __fns((unsigned)en.y, 0, p - pref_s[ep] + 1);
+        const unsigned sv = src_s[p];
+        const int ls = (int)(sv & 31u);
+        const int2 en = ent_s[sv >> 5];
         const int t = tbase + k;
         if (!mbar_wait_bounded(bar + t % NST, (unsigned)((t / NST) & 1))) timeout = true;
         near_source<M, float, LO, HI, PART>(slots + (size_t)(t % NST) * R, en.x * kGroup + ls,
