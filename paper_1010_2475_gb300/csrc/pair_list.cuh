@@ -339,7 +339,10 @@ __global__ void __launch_bounds__(W * 32, MINB)
   __syncthreads();  // every warp's (hi, lo) sums are in shared memory
   // (hi, lo) sums of the W warps -> FP64, this part's columns of block y:
   // column c (slot q) is summed by warp q mod W, one target per lane (the
-  // column of each slot is a compile-time constant)
+  // column of each slot is a compile-time constant).  The W pairs are added
+  // in FP32 with the rounding of every hi addition carried into lo, and only
+  // the final pair is widened: FP64 arithmetic is a small fraction of the
+  // FP32 rate here, and the CTA's tail runs alone on its SM.
   double* out = partial + (size_t)blockIdx.y * NB * n + (size_t)PN::B0 * n;
   const int jj = tg * kGroup + lane;
   static_for<0, NBL>([&](auto cc) {
@@ -347,12 +350,16 @@ __global__ void __launch_bounds__(W * 32, MINB)
     if constexpr (PC::in(c)) {
       constexpr int q = PC::slot(c);
       if (warp == q % W) {
-        double v = 0.0;
+        float h = 0.f, l = 0.f;
 #pragma unroll
-        for (int w = 0; w < W; ++w)
-          v += (double)acc_hi[(w * NS + q) * 32 + lane] +
-               (double)acc_lo[(w * NS + q) * 32 + lane];
-        if (jj < n) out[(size_t)c * n + jj] = v;
+        for (int w = 0; w < W; ++w) {
+          const float v = acc_hi[(w * NS + q) * 32 + lane];
+          const float sum = h + v;
+          const float bp = sum - h;
+          l += ((h - (sum - bp)) + (v - bp)) + acc_lo[(w * NS + q) * 32 + lane];
+          h = sum;
+        }
+        if (jj < n) out[(size_t)c * n + jj] = (double)h + (double)l;
       }
     }
   });
