@@ -126,6 +126,57 @@ def test_near_coincident_and_far_pairs(mm):
     assert rhs_error_rows(gM, oM, order, lam0) <= FP64_TOL
 
 
+def _loose_group_workload(order):
+    """A tight cluster of 32 particles (radius 0.1) and 32 spread from 0.3
+    to 8 along a spiral around it: the spread group's box reaches into the
+    cluster, so its list holds the cluster's sources, while its outer
+    targets sit at x = |s|^2 / (2 lambda^2) up to ~800 from them, beyond the
+    table form of the edge (x < 300): one warp then holds lanes on both
+    forms of the per-order branch."""
+    rng = np.random.default_rng(77)
+    r_in = 0.1 * np.sqrt(rng.uniform(size=32))
+    th_in = rng.uniform(0, 2 * np.pi, 32)
+    r_out = np.linspace(0.3, 8.0, 32)
+    th_out = np.linspace(0.0, 5 * np.pi, 32)
+    x = np.concatenate([np.stack([r_in * np.cos(th_in), r_in * np.sin(th_in)], 1),
+                        np.stack([r_out * np.cos(th_out), r_out * np.sin(th_out)], 1)])
+    K = (order + 1) * (order + 2) // 2
+    mom = rng.normal(size=(64, K)) * 0.02
+    mom[:, 0] = rng.normal(size=64)
+    mom[:, 1:3] = 0.0
+    return x, mom
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_near_list_lanes_on_both_edge_forms(mm, order, monkeypatch):
+    """Every compiled variant against the oracle when a near-listed group
+    mixes pairs below and above the table form's limit (mixed precision,
+    far field on), and the FP64 form at 1e-12."""
+    x, mom = _loose_group_workload(order)
+    lam0, nu, t = 0.2, 1e-3, 0.0
+    ox, oM = rhs_regrouped(x, mom, t, order, lam0, nu)
+    dx = x[32:, None, :] - x[None, :32, :]
+    xs = (dx ** 2).sum(-1) / (2 * lam0 ** 2)
+    assert xs.max() > 600.0 and xs.min() < 5.0  # both forms occur in the pairs
+    with mm.Context(order, lam0, nu, mm.MMVM_FP64) as ctx:
+        ctx.set_state(x, mom, t)
+        gx, gM = ctx.rhs()
+    assert vel_error_rows(gx, ox) <= FP64_TOL
+    assert rhs_error_rows(gM, oM, order, lam0) <= FP64_TOL
+    nd, nl = mm.pair_variant_counts(order)
+    assert nl >= 1
+    for v in range(nd + nl):
+        monkeypatch.setenv("MMVM_PAIR_VARIANT", str(v))
+        with mm.Context(order, lam0, nu, mm.MMVM_MIXED_FP32) as ctx:
+            ctx.set_state(x, mom, t)
+            gx, gM = ctx.rhs()
+            cfg = mm.mmvm_pair_config(ctx.handle)
+        assert cfg["variant"] == v
+        ev, em = cond_errors(gx, gM, ox, oM, x, mom, t, order, lam0, nu, np.arange(64))
+        assert ev <= mixed_rhs_tol(order), cfg
+        assert em <= mixed_rhs_tol(order), cfg
+
+
 def test_rk4_fp64_matches_oracle(mm):
     wl = mmvm_inputs.random_disk(n=24, order=3, radius=2.0, sigma=0.5, amp=0.03, moment_scale="absolute", seed=3)
     dt, nsteps = 0.02, 5
