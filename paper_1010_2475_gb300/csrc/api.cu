@@ -90,7 +90,7 @@ struct mmvm_ctx {
   DevBuf<unsigned long long> counts;
   bool far = false;    // FP32 and not MMVM_FLAG_NO_FAR_FIELD: sort + far-field tiles
   bool high = false;   // single particle through the separable self term (self_high.cu)
-  DevBuf<double> sbinom, sg, sscr;  // its factor tables and scratch
+  DevBuf<double> sbinom, sg, scg, sscr;  // its factor tables and scratch
   DevBuf<double> dpts, dval, dring;  // diagnostics: points, values, ring sums
   DevBuf<double> dk;                  // adaptive steps: 7 stage derivatives
   DevBuf<unsigned long long> derr;    // adaptive steps: error of the step (bits)
@@ -330,6 +330,7 @@ int enqueue_rhs(mmvm_ctx* c, int mode, const double* xin, const double* min_, do
     H.psi0 = c->psi0.p;
     H.binom = c->sbinom.p;
     H.g = c->sg.p;
+    H.cg = c->scg.p;
     H.lam0sq = lam0sq;
     H.four_nu = four_nu;
     H.t_dev = c->t_dev();
@@ -740,10 +741,13 @@ int mmvm_create(const mmvm_config* cfg, mmvm_ctx** out) {
     mmvm::SeparableTables ST = mmvm::build_separable_tables(c->M);
     if ((e = c->sbinom.ensure(ST.binom.size())) != cudaSuccess ||
         (e = c->sg.ensure(ST.g.size())) != cudaSuccess ||
+        (e = c->scg.ensure(ST.cg.size())) != cudaSuccess ||
         (e = c->sscr.ensure(mmvm::self_high_scratch_doubles(c->M))) != cudaSuccess ||
         (e = cudaMemcpy(c->sbinom.p, ST.binom.data(), ST.binom.size() * sizeof(double),
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(c->sg.p, ST.g.data(), ST.g.size() * sizeof(double),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->scg.p, ST.cg.data(), ST.cg.size() * sizeof(double),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(cuda_fail(e, "separable tables"));
   }
@@ -784,7 +788,7 @@ void mmvm_destroy(mmvm_ctx* c) {
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
   for (auto* b : {&c->x, &c->m, &c->xs, &c->ms, &c->xsum, &c->msum, &c->rdx, &c->rdm, &c->scal,
-                  &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->sscr, &c->dpts, &c->dval, &c->dring, &c->dk,
+                  &c->partial, &c->e_c, &c->psi0, &c->sbinom, &c->sg, &c->scg, &c->sscr, &c->dpts, &c->dval, &c->dring, &c->dk,
                   &c->fpart})
     b->release();
   c->tnodes.release();

@@ -88,6 +88,7 @@ struct SelfHighArgs {
   const double* psi0 = nullptr;   // jet at the origin, |alpha| <= 3M (tables.h)
   const double* binom = nullptr;  // (M+1) x (M+1): C(l, q)
   const double* g = nullptr;      // M+1: g(j) = 4^{-j} / j!
+  const double* cg = nullptr;     // (M+1)^3: C(l, q) g(k - q) at ((l (M+1) + k) (M+1) + q)
   double* at = nullptr;           // scratch (set by the launcher)
   double* Psi = nullptr;
   double *U1 = nullptr, *U2 = nullptr, *V1 = nullptr, *V2 = nullptr;

@@ -22,7 +22,8 @@
 //   pass 2  V[k2, l1, b1] = sum_l2 (-1)^{l2} a_{l1,l2} U[k2, l2, b1]     (l1 + l2 <= M)
 //   pass 3  R_k = (-1)^{|k|} sum_l1 (-1)^{l1} sum_i C(l1,i) g(k1(-1)-i)
 //                 (-V^I[k2, l1, beta1] + V^II[k2, l1, beta1])
-// for about 4.6e7 multiply-adds at M = 60 instead of about 1e9.  Every factor
+// for about 4.6e7 multiply-adds at M = 60 instead of about 1e9 (the products
+// C g come from a host table, so each term is one multiply-add).  Every factor
 // g is at most 1, so the intermediate sums stay far inside the FP64 range
 // (the jet psi0 reaches ~1e190 at order 3M = 180; binomials ~1e17).  Only
 // terms with |beta| <= 2M exist (|k|, |l| <= M); pass 1 skips the rest.
@@ -78,17 +79,18 @@ __global__ void self_pass1_kernel(SelfHighArgs A) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (M + 1) * (M + 1) * W) return;
   const int b1 = idx % W, l2 = (idx / W) % (M + 1), k2 = idx / (W * (M + 1));
-  const double* Cl = A.binom + l2 * (M + 1);
+  // C(l2, q) g(k2 - q) and C(l2, q) g(k2 - 1 - q), q = 0, 1, ...
+  const double* c1 = A.cg + ((size_t)l2 * (M + 1) + k2) * (M + 1);
   double u1 = 0.0, u2 = 0.0;
   for (int q = 0; q <= min(l2, k2); ++q) {
     const int bb2 = k2 + l2 - 2 * q + 1;
-    if (b1 + bb2 <= 2 * M) u1 = fma(Cl[q] * A.g[k2 - q], A.Psi[bcol(b1, bb2)], u1);
+    if (b1 + bb2 <= 2 * M) u1 = fma(c1[q], A.Psi[bcol(b1, bb2)], u1);
   }
   if (k2 >= 1) {
+    const double* c2 = c1 - (M + 1);
     for (int q = 0; q <= min(l2, k2 - 1); ++q) {
       const int bb2 = k2 + l2 - 2 * q - 1;
-      if (b1 + bb2 <= 2 * M && b1 + bb2 >= 1)
-        u2 = fma(Cl[q] * A.g[k2 - 1 - q], A.Psi[bcol(b1, bb2)], u2);
+      if (b1 + bb2 <= 2 * M && b1 + bb2 >= 1) u2 = fma(c2[q], A.Psi[bcol(b1, bb2)], u2);
     }
   }
   A.U1[idx] = u1;
@@ -133,15 +135,18 @@ __global__ void self_pass3_kernel(SelfHighArgs A) {
   const double* v2 = A.V2 + (size_t)k2 * (M + 1) * W;
   double r = 0.0;
   for (int l1 = lane; l1 <= M; l1 += 32) {
-    const double* Cl = A.binom + l1 * (M + 1);
+    // C(l1, i) g(k1 - i) and C(l1, i) g(k1 - 1 - i), i = 0, 1, ...
+    const double* cb = A.cg + ((size_t)l1 * (M + 1) + k1) * (M + 1);
     double s = 0.0;
-    if (k1 >= 1)
+    if (k1 >= 1) {
+      const double* ca = cb - (M + 1);
       for (int i = 0; i <= min(l1, k1 - 1); ++i)
-        s = fma(-Cl[i] * A.g[k1 - 1 - i], v1[(size_t)l1 * W + k1 + l1 - 2 * i - 1], s);
+        s = fma(-ca[i], v1[(size_t)l1 * W + k1 + l1 - 2 * i - 1], s);
+    }
     if (k2 >= 1)
       for (int i = 0; i <= min(l1, k1); ++i) {
         const int bb1 = k1 + l1 - 2 * i + 1;
-        if (bb1 < W) s = fma(Cl[i] * A.g[k1 - i], v2[(size_t)l1 * W + bb1], s);
+        if (bb1 < W) s = fma(cb[i], v2[(size_t)l1 * W + bb1], s);
       }
     r += (l1 & 1) ? -s : s;
   }

@@ -1,6 +1,7 @@
 // Host generation of the FP64 finish tables (see tables.h for the formulas).
 #include "tables.h"
 
+#include <algorithm>
 #include <map>
 #include <tuple>
 
@@ -101,6 +102,12 @@ SeparableTables build_separable_tables(int M) {
     for (int b = 0; b <= a; ++b) t.binom[(size_t)a * (M + 1) + b] = (double)binoml(a, b);
     t.g[a] = (double)(pow4l(-a) / factl(a));
   }
+  const size_t W = (size_t)M + 1;
+  t.cg.assign(W * W * W, 0.0);
+  for (int l = 0; l <= M; ++l)
+    for (int k = 0; k <= M; ++k)
+      for (int q = 0; q <= std::min(l, k); ++q)
+        t.cg[((size_t)l * W + k) * W + q] = t.binom[(size_t)l * W + q] * t.g[k - q];
   return t;
 }
 

@@ -40,9 +40,11 @@ struct FinishTables {
 FinishTables build_finish_tables(int M, bool entries = true);
 
 // Factors of the separable single-particle path (self_high.cu): binom is
-// row-major (M+1) x (M+1), binom[l][q] = C(l, q); g[j] = 4^{-j} / j!, j <= M.
+// row-major (M+1) x (M+1), binom[l][q] = C(l, q); g[j] = 4^{-j} / j!, j <= M;
+// cg[(l (M+1) + k) (M+1) + q] = binom[l][q] * g[k - q] (the FP64 product, 0
+// for q > min(l, k)), so that the passes do one multiply-add per term.
 struct SeparableTables {
-  std::vector<double> binom, g;
+  std::vector<double> binom, g, cg;
 };
 SeparableTables build_separable_tables(int M);
 
